@@ -1,0 +1,343 @@
+"""Benchmark: batched exact MVC on one GB300 (and weak-scaled replicas on N GPUs).
+
+Workload (one step): 4096 independent Erdos-Renyi graphs, n ~ U{20..120}, p ~ U[0.05, 0.30],
+graph g drawn from seed g (plus rank * 4096 under torchrun), packed CSR int32, solved by one
+persistent launch of the whole hot path: CSR validation, greedy bound, traversal (reduction rules,
+stop check, argmax branch, local stacks + device worklist, termination), results back.
+
+Reported:
+  value      solves/s with the packed CSR resident in HBM (CUDA events on the call's stream)
+  e2e        solves/s through the C ABI with pinned host buffers (H2D + D2H inside the timing)
+  nodes/s, the traversal kernel's roofline, per-request plain launches on the same GPU, the CPU
+  oracle on a bounded sample of the same workload, SM clocks sampled during the timed region.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "search-tree nodes/sec and solves/sec (p50/p99 latency) vs plain launches; % L2/HBM roofline"
+NUM_GRAPHS = 4096
+L2_FLUSH_BYTES = 256 << 20
+CPU_SAMPLE_GRAPHS = 128
+PLAIN_SAMPLE_GRAPHS = 512
+# Kernels the library launches per batched call: validation, worklist init, greedy, traversal.
+KERNELS_PER_STEP = 4
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--graphs", type=int, default=NUM_GRAPHS)
+    ap.add_argument("--no-plain", action="store_true", help="skip the per-request plain-launch leg")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline leg")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(rank: int, count: int):
+    from paper_2204_10402_gb300 import graphs as G
+    return G.batch_gnp(count, first_seed=rank * NUM_GRAPHS)
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------------------------------------
+# CPU oracle legs (test infrastructure, timed as the reported baseline)
+# ------------------------------------------------------------------------------------------------
+
+def _oracle_sizes(args):
+    import oracle
+    from paper_2204_10402_gb300 import graphs as G
+    seeds = args
+    out = []
+    for s in seeds:
+        n, p = G.batch_gnp_params(s)
+        out.append(oracle.mvc(G.gnp(n, p, s, draw_offset=2))[0])
+    return out
+
+
+def oracle_solves(seeds: list, cores: int):
+    """Solves the given batch graphs with the oracle on `cores` processes; returns seconds."""
+    import oracle
+    oracle.build()
+    if cores <= 1:
+        t0 = time.perf_counter()
+        _oracle_sizes(seeds)
+        return time.perf_counter() - t0
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    chunks = [seeds[i::cores] for i in range(cores)]
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_sizes, [[0]] * cores)  # warm the workers (import + load) before timing
+        t0 = time.perf_counter()
+        pool.map(_oracle_sizes, chunks)
+        return time.perf_counter() - t0
+
+
+def run_reference(a):
+    """The oracle as the reference arm: each step solves a bounded sample of the same workload
+    (24 graphs, cycling through the 4096) on all host cores."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    cores = min(os.cpu_count() or 1, 16)
+    per_step = 24
+    for w in range(a.warmup):
+        oracle_solves([(w * per_step + i) % NUM_GRAPHS for i in range(per_step)], cores)
+    t = 0.0
+    done = 0
+    for s in range(a.steps):
+        base = (a.warmup + s) * per_step
+        t += oracle_solves([(base + i) % NUM_GRAPHS for i in range(per_step)], cores)
+        done += per_step
+    v = done / t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": a.gpus,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1000 * t / a.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": f"batched MVC, {NUM_GRAPHS} G(n,p) graphs n~U{{20..120}} p~U[0.05,0.30] (seeded)",
+                   "graphs_per_step": per_step, "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": v, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{per_step} graphs per step, cycling through the batch"},
+        "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------------------
+# GPU leg
+# ------------------------------------------------------------------------------------------------
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def run_ours(a):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2204_10402_gb300 as vc
+    from paper_2204_10402_gb300 import build
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    vc.load()
+
+    b = workload(rank, a.graphs)
+    off_d = torch.from_numpy(b.offsets).to(dev)
+    nbr_d = torch.from_numpy(b.neighbors).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    total_n = int(b.vtx[-1])
+
+    def step_device():
+        sizes, covers, st = vc.mvc_batch(b.vtx, b.edge, off_d, nbr_d, stream=stream)
+        return sizes, st
+
+    for _ in range(a.warmup):
+        step_device()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+
+    # ---- timed region: K steps, inputs resident in HBM, L2 flushed between steps ----
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    kernel_ms, stats = [], []
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        for i in range(a.steps):
+            flush.fill_(i)
+            ev[i][0].record(stream)
+            sizes, st = step_device()
+            ev[i][1].record(stream)
+            kernel_ms.append(st["kernel_ms"])
+            stats.append(st)
+        torch.cuda.synchronize()
+    step_ms = [s.elapsed_time(e) for s, e in ev]
+    t_local = sum(step_ms) / 1000.0
+    t_max = t_local
+    if world > 1:
+        tt = torch.tensor([t_local], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+        dist.barrier()
+    solves = a.graphs * a.steps * world
+    value = solves / t_max
+    nodes = sum(s["nodes_visited"] for s in stats)
+
+    # ---- e2e: the same call with pinned host buffers (H2D + D2H inside the timing) ----
+    off_h = torch.from_numpy(b.offsets).pin_memory()
+    nbr_h = torch.from_numpy(b.neighbors).pin_memory()
+    e2e_ms = []
+    for i in range(a.steps):
+        flush.fill_(i)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sizes_h, covers_h, st_h = vc.mvc_batch(b.vtx, b.edge, off_h.numpy(), nbr_h.numpy(), stream=stream)
+        e2e_ms.append(1000 * (time.perf_counter() - t0))
+    G = a.graphs
+    # bytes the library copies per call: packed CSR + problem table + expected lengths up; problem
+    # table, control block, per-SM counters and the Σn cover masks down
+    h2d = int(b.offsets.nbytes + b.neighbors.nbytes + G * 64 + G * 8)
+    d2h = int(G * 64 + 128 + 1024 * 8 + total_n * 4)
+    e2e_value = solves / world / (sum(e2e_ms) / 1000.0) * world if e2e_ms else None
+
+    out = None
+    if rank == 0:
+        # ---- roofline of the traversal kernel: algorithmic bytes / its event-timed duration ----
+        hbm, peak_kind = peaks()
+        alg_bytes = [s["entry_bytes_moved"] + 4 * s["csr_words"] for s in stats]
+        ach = [bb / (km * 1e-3) / 1e9 for bb, km in zip(alg_bytes, kernel_ms) if km > 0]
+        achieved = statistics.mean(ach) if ach else 0.0
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                    "frac": achieved / hbm, "traffic": None, "peak_kind": peak_kind,
+                    "kernel": "traverse_kernel", "kernel_ms_mean": statistics.mean(kernel_ms),
+                    "alg_bytes_per_launch": statistics.mean(alg_bytes)}
+        line = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": 1000 * t_max / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": f"batched MVC, {G} G(n,p) graphs per GPU, n~U{{20..120}}, p~U[0.05,0.30], "
+                                   "seed = graph index (+ rank*4096), packed CSR int32",
+                       "graphs_per_step": G, "sum_n": total_n, "sum_2m": int(b.edge[-1]),
+                       "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)",
+                       "parallelism": f"replicas x{world}",
+                       "variant": {"width": stats[0]["width"], "worker_threads": stats[0]["worker_threads"],
+                                   "workers": stats[0]["workers"]}},
+            "nodes_per_s": nodes * world / t_max,
+            "nodes_per_step": nodes / a.steps,
+            "latency_ms": {"p50": statistics.median(step_ms), "p99": float(np.percentile(step_ms, 99)),
+                           "note": "every graph of a step completes with the step"},
+            "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": KERNELS_PER_STEP * a.steps,
+            "roofline": roofline,
+        }
+        if not a.no_plain:
+            line["vs_plain_launches"] = plain_launches(vc, b, dev, stream, value)
+        clocks = clk.summary()
+        line["clocks"] = clocks
+        if not a.no_cpu and world == 1:
+            seeds = list(range(min(CPU_SAMPLE_GRAPHS, G)))
+            secs = oracle_solves(seeds, 1)
+            line["cpu_baseline"] = {"value": len(seeds) / secs, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                                    "sample": f"first {len(seeds)} graphs of the batch, one core"}
+        out = line
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return out
+
+
+def plain_launches(vc, b, dev, stream, batched_value):
+    """Per-request plain launches: one vc_mvc call per graph (device-resident CSR), same GPU."""
+    import torch
+    cnt = min(PLAIN_SAMPLE_GRAPHS, len(b.graphs))
+    offs = [torch.from_numpy(g.offsets).to(dev) for g in b.graphs[:cnt]]
+    nbrs = [torch.from_numpy(g.neighbors if g.neighbors.size else np.zeros(1, np.int32)).to(dev)
+            for g in b.graphs[:cnt]]
+    for i in range(min(8, cnt)):
+        vc.mvc(offs[i], nbrs[i], stream=stream, want_cover=False)
+    torch.cuda.synchronize()
+    lat = []
+    t0 = time.perf_counter()
+    for i in range(cnt):
+        s = time.perf_counter()
+        vc.mvc(offs[i], nbrs[i], stream=stream, want_cover=False)
+        lat.append(1000 * (time.perf_counter() - s))
+    total = time.perf_counter() - t0
+    plain = cnt / total
+    return {"plain_solves_per_s": plain, "batched_over_plain": batched_value / plain,
+            "plain_latency_ms": {"p50": statistics.median(lat), "p99": float(np.percentile(lat, 99))},
+            "sample": f"first {cnt} graphs, one synchronous vc_mvc call each"}
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,157 @@
+/*
+ * vc.h - C ABI of libvc: exact vertex cover on one GB300 (sm_103a) by data-parallel traversal of
+ * the branch-and-reduce search tree.
+ *
+ * Method: Yamout, Barada, Jaljuli, Mouawad, El Hajj, "Parallel Vertex Cover Algorithms on GPUs"
+ * (arXiv 2204.10402).
+ *   - Problems (Sec. II-A): MVC finds a minimum vertex cover; PVC decides whether a cover of size
+ *     <= k exists.
+ *   - Search (Sec. II-B): at every tree node the degree-one, degree-two-triangle and high-degree
+ *     reduction rules run to a fixpoint, then a stop check, then a solution check, then a branch on
+ *     the maximum-degree vertex v into "v into S" and "N(v) into S".  The incumbent starts at the
+ *     greedy upper bound.
+ *   - Parallel traversal (Sec. IV-A, IV-C): each worker (a CUDA thread block) walks a sub-tree from
+ *     a local stack and donates the N(v) child to a device-wide worklist while the worklist holds
+ *     fewer entries than a threshold; idle workers take entries from the worklist; the search ends
+ *     when the worklist is empty and every worker is idle.
+ *   - State (Sec. IV-B): an intermediate graph is a degree array (one entry per original vertex,
+ *     -1 once the vertex is in S) plus |S| and the remaining edge count, next to one read-only CSR.
+ *
+ * Graph input (all entry points): an undirected simple graph in CSR form.  offsets has n+1
+ * int32 entries with offsets[0] = 0 and offsets[n] = 2m; neighbors has 2m int32 entries; each
+ * undirected edge appears in both endpoint lists; every list is sorted strictly ascending; no
+ * self-loops.  A graph that breaks any of these rules is rejected with VC_EINVAL (checked on the
+ * GPU before any search).
+ *
+ * Memory: the caller owns every input and output buffer.  Host pointers are accepted when
+ * on_device = 0 and device pointers (for example torch CUDA tensors) when on_device = 1; the
+ * cover output follows the same flag, scalar outputs are always host pointers.  The library keeps
+ * no pointer to caller memory after a call returns.  Device scratch (the copy of the graph,
+ * stacks, worklist, counters) is allocated with cudaMalloc on first use, cached per device, grown
+ * when a larger problem arrives, and released by vc_release() or at process exit.
+ *
+ * Streams: every call enqueues its work on `stream` (a cudaStream_t; NULL = the legacy default
+ * stream), waits for that stream, and returns.  Calls from several host threads are serialised by
+ * an internal lock.
+ *
+ * Errors: every function returns VC_OK (0) or a negative code below; on error the outputs are
+ * unspecified.  vc_strerror() names a code.
+ */
+#ifndef VC_H
+#define VC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VC_OK 0
+#define VC_EINVAL (-1)      /* bad argument or malformed CSR */
+#define VC_ENOMEM (-2)      /* device or pinned host allocation failed */
+#define VC_ETIMEOUT (-3)    /* a device wait ran past its time limit; the search was abandoned */
+#define VC_ESTACK (-4)      /* a local stack would have grown past its provisioned depth */
+#define VC_ECUDA (-5)       /* a CUDA runtime call failed */
+#define VC_ECANCELLED (-6)  /* the caller's cancel flag was raised */
+
+/* An undirected graph in CSR form (see the input rules above). */
+typedef struct {
+    int32_t n;                 /* number of vertices, >= 0 */
+    const int32_t *offsets;    /* n+1 entries */
+    const int32_t *neighbors;  /* offsets[n] entries */
+    int32_t on_device;         /* 0: host pointers, 1: device pointers */
+} vc_graph;
+
+/* Launch configuration.  Zero in any field selects the library's choice for it. */
+typedef struct {
+    int32_t worker_threads;     /* threads per worker (one worker = one thread block): 32..512, power of 2 */
+    int32_t num_workers;        /* persistent workers (thread blocks); 0 = SMs x resident blocks per SM */
+    int32_t width;              /* degree-array entry width in bits: 16 or 32 */
+    int32_t worklist_capacity;  /* worklist entries */
+    float donate_threshold;     /* donate while the worklist holds fewer than this fraction of its capacity */
+    int64_t idle_timeout_ns;    /* an idle worker that finds no work for this long aborts with VC_ETIMEOUT (default 20 s) */
+    int32_t skip_validation;    /* 1: trust the CSR and skip the device check */
+    int32_t max_stack_bytes;    /* unused, reserved (0) */
+    const volatile int32_t *cancel;  /* optional host-mapped or device flag; nonzero aborts with VC_ECANCELLED */
+} vc_config;
+
+/* Counters of one call (all filled by the device except kernel_ms and the sizes). */
+typedef struct {
+    int64_t nodes_visited;      /* search-tree nodes expanded by the traversal kernel */
+    int64_t stack_pushes;       /* N(v) children pushed on a local stack */
+    int64_t stack_pops;         /* local stack pops */
+    int64_t donations;          /* N(v) children put on the worklist */
+    int64_t worklist_pops;      /* worklist entries taken */
+    int64_t rule_passes;        /* reduction-rule passes (each scans one degree array) */
+    int64_t csr_words;          /* CSR neighbour words read during the search */
+    int64_t entry_bytes_moved;  /* degree-array entry bytes copied between shared and global memory */
+    int32_t max_depth;          /* deepest local stack seen */
+    int32_t greedy_ub;          /* greedy upper bound (single-graph calls; batch: sum over graphs) */
+    int32_t workers;            /* persistent workers launched */
+    int32_t worker_threads;     /* threads per worker */
+    int32_t width;              /* 16 or 32 */
+    int32_t status;             /* device status word (VC_OK or an error code) */
+    float kernel_ms;            /* traversal kernel time (CUDA events on the call's stream) */
+    float total_ms;             /* whole call (validation, greedy, traversal, copies) */
+} vc_stats;
+
+/* Minimum Vertex Cover (Sec. II-A, II-B, IV).
+ * cover_out: n int32 entries (host or device per g->on_device), receives 1 for vertices of a
+ * minimum cover and 0 elsewhere; may be NULL.  *cover_size_out receives the minimum size.
+ * cfg and stats may be NULL. */
+int vc_mvc(const vc_graph *g, const vc_config *cfg, void *stream,
+           int32_t *cover_out, int32_t *cover_size_out, vc_stats *stats);
+
+/* Parameterized Vertex Cover (Sec. II-A, II-B last paragraph, IV-A last paragraph).
+ * *found_out = 1 iff a cover of size <= k exists; then cover_out (n entries, may be NULL)
+ * receives such a cover as a 0/1 mask and *cover_size_out its size (else -1).  k < 0 is answered
+ * "no" without touching the GPU.  When the greedy bound is already <= k the answer is "yes" with
+ * the greedy cover and no search runs. */
+int vc_pvc(const vc_graph *g, int32_t k, const vc_config *cfg, void *stream,
+           int32_t *found_out, int32_t *cover_out, int32_t *cover_size_out, vc_stats *stats);
+
+/* Batched MVC: num_graphs independent graphs solved by one persistent launch whose worklist
+ * entries carry their graph's index.  Graph g has graph_vtx_offsets[g+1]-graph_vtx_offsets[g]
+ * vertices; its own n_g+1 offsets (starting at 0) sit at packed_offsets[graph_vtx_offsets[g] + g],
+ * its neighbours (numbered 0..n_g-1) at packed_neighbors[graph_edge_offsets[g] ...].
+ * sizes_out (host, num_graphs) receives each minimum size; covers_out (Σ n_g entries laid out by
+ * graph_vtx_offsets, host or device per on_device, may be NULL) receives 0/1 cover masks.
+ * graph_vtx_offsets and graph_edge_offsets are host arrays of num_graphs+1 entries. */
+int vc_mvc_batch(int32_t num_graphs, const int32_t *graph_vtx_offsets, const int32_t *graph_edge_offsets,
+                 const int32_t *packed_offsets, const int32_t *packed_neighbors, int32_t on_device,
+                 const vc_config *cfg, void *stream, int32_t *sizes_out, int32_t *covers_out,
+                 vc_stats *stats);
+
+/* Greedy upper bound on the GPU (Sec. II-B): repeat { degree-one and degree-two-triangle rules to a
+ * fixpoint; stop when edgeless; put the maximum-degree vertex (lowest id on ties) into S }.
+ * *size_out receives |S|; cover_out (n entries, may be NULL) the cover mask. */
+int vc_greedy(const vc_graph *g, const vc_config *cfg, void *stream, int32_t *cover_out, int32_t *size_out);
+
+/* One tree node's reduction on the GPU (Sec. II-B rules with the Sec. IV-D tie-breaks), for
+ * testing.  deg (n entries, host or device per g->on_device) holds the degree array (-1 = in S) and
+ * is reduced in place; *S and *m hold |S| and the edge count and are updated.  problem: 0 = MVC
+ * (bound = best), 1 = PVC (bound = k).  rules: bit 0 degree-one, bit 1 degree-two-triangle,
+ * bit 2 high-degree.  *pruned_out receives 1 iff the stop check prunes the reduced node.
+ * Every rule pass is one simultaneous round: vertices that meet the rule at the start of the pass
+ * are found, then all of them enter S together. */
+int vc_reduce_node(const vc_graph *g, int32_t *deg, int32_t *S, int32_t *m, int32_t problem,
+                   int32_t bound, int32_t rules, const vc_config *cfg, void *stream, int32_t *pruned_out);
+
+/* Per-SM search-tree node counts of the last traversal on the current device (Sec. V-C load
+ * measure): counts_out receives min(capacity, SM count) entries; returns the SM count or an
+ * error code. */
+int vc_last_sm_nodes(int64_t *counts_out, int32_t capacity);
+
+/* Releases the cached device scratch of the current device. */
+int vc_release(void);
+/* Short name of a status code. */
+const char *vc_strerror(int code);
+/* Library version: major * 10000 + minor * 100 + patch. */
+int vc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VC_H */

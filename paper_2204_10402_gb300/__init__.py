@@ -1,0 +1,300 @@
+"""Python binding of libvc (include/vc.h): exact vertex cover on a GB300 GPU.
+
+Argument marshalling only: every step of the search runs in the CUDA kernels of ``libvc.so``.
+Graphs are CSR arrays (``offsets`` n+1, ``neighbors`` 2m, int32) given as numpy arrays (host) or
+torch CUDA tensors (device).  If ``libvc.so`` has not been built, importing a solver raises; there
+is no CPU fallback.
+
+    mvc(offsets, neighbors)            -> Answer(size, cover, stats)
+    pvc(offsets, neighbors, k)         -> Answer(found, cover, stats)
+    mvc_batch(batch)                   -> (sizes, covers, stats)
+    greedy(offsets, neighbors)         -> (size, cover)
+    reduce_node(offsets, neighbors, deg, S, m, problem, bound, rules) -> (deg, S, m, pruned)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libvc.so")
+
+VC_OK, VC_EINVAL, VC_ENOMEM, VC_ETIMEOUT, VC_ESTACK, VC_ECUDA, VC_ECANCELLED = 0, -1, -2, -3, -4, -5, -6
+MVC, PVC = 0, 1
+RULE_DEG1, RULE_DEG2TRI, RULE_HIGH, RULE_ALL = 1, 2, 4, 7
+
+EXPORTED = ["vc_mvc", "vc_pvc", "vc_mvc_batch", "vc_greedy", "vc_reduce_node", "vc_last_sm_nodes",
+            "vc_release", "vc_strerror", "vc_version"]
+
+
+class VCError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where} failed: {_strerror(code)} ({code})")
+
+
+class Graph(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("offsets", ctypes.c_void_p), ("neighbors", ctypes.c_void_p),
+                ("on_device", ctypes.c_int32)]
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("worker_threads", ctypes.c_int32), ("num_workers", ctypes.c_int32),
+                ("width", ctypes.c_int32), ("worklist_capacity", ctypes.c_int32),
+                ("donate_threshold", ctypes.c_float), ("idle_timeout_ns", ctypes.c_int64),
+                ("skip_validation", ctypes.c_int32), ("max_stack_bytes", ctypes.c_int32),
+                ("cancel", ctypes.c_void_p)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("nodes_visited", ctypes.c_int64), ("stack_pushes", ctypes.c_int64),
+                ("stack_pops", ctypes.c_int64), ("donations", ctypes.c_int64),
+                ("worklist_pops", ctypes.c_int64), ("rule_passes", ctypes.c_int64),
+                ("csr_words", ctypes.c_int64), ("entry_bytes_moved", ctypes.c_int64),
+                ("max_depth", ctypes.c_int32), ("greedy_ub", ctypes.c_int32), ("workers", ctypes.c_int32),
+                ("worker_threads", ctypes.c_int32), ("width", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("kernel_ms", ctypes.c_float), ("total_ms", ctypes.c_float)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return LIB_PATH
+
+
+def load(path: str | None = None):
+    """Loads libvc.so (raising if it is missing) and declares the C signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise ImportError(f"libvc.so not built at {path}; run python -m paper_2204_10402_gb300.build")
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    i32, i64 = ctypes.c_int32, ctypes.c_int64
+    gp, cp, sp = ctypes.POINTER(Graph), ctypes.POINTER(Config), ctypes.POINTER(Stats)
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    lib.vc_mvc.argtypes = [gp, cp, P, P, i32p, sp]
+    lib.vc_pvc.argtypes = [gp, i32, cp, P, i32p, P, i32p, sp]
+    lib.vc_mvc_batch.argtypes = [i32, P, P, P, P, i32, cp, P, P, P, sp]
+    lib.vc_greedy.argtypes = [gp, cp, P, P, i32p]
+    lib.vc_reduce_node.argtypes = [gp, P, i32p, i32p, i32, i32, i32, cp, P, i32p]
+    lib.vc_last_sm_nodes.argtypes = [P, i32]
+    lib.vc_release.argtypes = []
+    lib.vc_strerror.argtypes = [ctypes.c_int]
+    lib.vc_strerror.restype = ctypes.c_char_p
+    lib.vc_version.argtypes = []
+    for name in ("vc_mvc", "vc_pvc", "vc_mvc_batch", "vc_greedy", "vc_reduce_node", "vc_last_sm_nodes",
+                 "vc_release", "vc_version"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _strerror(code: int) -> str:
+    try:
+        return load().vc_strerror(code).decode()
+    except Exception:
+        return str(code)
+
+
+def _check(rc: int, where: str):
+    if rc != VC_OK:
+        raise VCError(rc, where)
+
+
+# ---------------------------------------------------------------------------------------------
+# argument marshalling
+# ---------------------------------------------------------------------------------------------
+
+def _is_cuda_tensor(x) -> bool:
+    return hasattr(x, "is_cuda") and bool(getattr(x, "is_cuda"))
+
+
+def _host_i32(x) -> np.ndarray:
+    if hasattr(x, "detach"):
+        x = x.detach().cpu().numpy()
+    return np.ascontiguousarray(np.asarray(x), dtype=np.int32)
+
+
+def _ptr(x) -> int:
+    if _is_cuda_tensor(x):
+        return int(x.data_ptr())
+    return int(x.ctypes.data)
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return int(torch.cuda.current_stream().cuda_stream)
+        except Exception:
+            pass
+        return 0
+    if hasattr(stream, "cuda_stream"):
+        return int(stream.cuda_stream)
+    return int(stream)
+
+
+def make_config(**kw) -> Config:
+    c = Config()
+    for k, v in kw.items():
+        if v is None:
+            continue
+        if k == "cancel":
+            c.cancel = v
+        else:
+            setattr(c, k, v)
+    return c
+
+
+def _graph(offsets, neighbors):
+    """Returns (Graph, keepalive) for host numpy or CUDA tensor CSR arrays."""
+    if _is_cuda_tensor(offsets):
+        import torch
+        assert offsets.dtype == torch.int32 and neighbors.dtype == torch.int32, "CSR tensors must be int32"
+        offsets = offsets.contiguous()
+        neighbors = neighbors.contiguous()
+        n = offsets.numel() - 1
+        nb = neighbors if neighbors.numel() > 0 else torch.zeros(1, dtype=torch.int32, device=offsets.device)
+        return Graph(n, offsets.data_ptr(), nb.data_ptr(), 1), (offsets, nb)
+    off = _host_i32(offsets)
+    nbr = _host_i32(neighbors)
+    if nbr.size == 0:
+        nbr = np.zeros(1, dtype=np.int32)
+    return Graph(off.size - 1, off.ctypes.data, nbr.ctypes.data, 0), (off, nbr)
+
+
+def _cover_buffer(g: Graph, like):
+    if g.on_device:
+        import torch
+        return torch.empty(max(g.n, 1), dtype=torch.int32, device=like.device)
+    return np.zeros(max(g.n, 1), dtype=np.int32)
+
+
+@dataclass
+class Answer:
+    value: int          # MVC: minimum size; PVC: 1 if a cover of size <= k exists
+    cover: object       # 0/1 mask (numpy array, or torch tensor for device inputs), None if none
+    cover_size: int
+    stats: dict
+
+
+def mvc(offsets, neighbors, config: Config | None = None, stream=None, want_cover: bool = True) -> Answer:
+    """Minimum vertex cover (Sec. II-A) of one graph."""
+    lib = load()
+    g, keep = _graph(offsets, neighbors)
+    cover = _cover_buffer(g, offsets) if want_cover else None
+    size = ctypes.c_int32(-1)
+    st = Stats()
+    rc = lib.vc_mvc(ctypes.byref(g), ctypes.byref(config) if config else None, _stream(stream),
+                    _ptr(cover) if cover is not None else None, ctypes.byref(size), ctypes.byref(st))
+    _check(rc, "vc_mvc")
+    if cover is not None:
+        cover = cover[: g.n]
+    return Answer(int(size.value), cover, int(size.value), st.as_dict())
+
+
+def pvc(offsets, neighbors, k: int, config: Config | None = None, stream=None, want_cover: bool = True) -> Answer:
+    """Parameterized vertex cover (Sec. II-A): is there a cover of size <= k?"""
+    lib = load()
+    g, keep = _graph(offsets, neighbors)
+    cover = _cover_buffer(g, offsets) if want_cover else None
+    found = ctypes.c_int32(0)
+    csize = ctypes.c_int32(-1)
+    st = Stats()
+    rc = lib.vc_pvc(ctypes.byref(g), int(k), ctypes.byref(config) if config else None, _stream(stream),
+                    ctypes.byref(found), _ptr(cover) if cover is not None else None, ctypes.byref(csize),
+                    ctypes.byref(st))
+    _check(rc, "vc_pvc")
+    if cover is not None:
+        cover = cover[: g.n] if found.value else None
+    return Answer(int(found.value), cover, int(csize.value), st.as_dict())
+
+
+def mvc_batch(vtx, edge, offsets, neighbors, config: Config | None = None, stream=None,
+              want_covers: bool = True):
+    """Batched MVC over packed graphs (see graphs.pack for the layout).  ``vtx`` and ``edge`` are
+    host arrays of G+1 prefix sums; ``offsets``/``neighbors`` host arrays or CUDA tensors."""
+    lib = load()
+    vtx = _host_i32(vtx)
+    edge = _host_i32(edge)
+    G = vtx.size - 1
+    on_dev = _is_cuda_tensor(offsets)
+    if on_dev:
+        import torch
+        off_t = offsets.contiguous()
+        nb_t = neighbors.contiguous() if neighbors.numel() else torch.zeros(1, dtype=torch.int32, device=offsets.device)
+        off_p, nb_p = off_t.data_ptr(), nb_t.data_ptr()
+        covers = torch.empty(max(int(vtx[-1]), 1), dtype=torch.int32, device=offsets.device) if want_covers else None
+    else:
+        off_t = _host_i32(offsets)
+        nb_t = _host_i32(neighbors)
+        if nb_t.size == 0:
+            nb_t = np.zeros(1, dtype=np.int32)
+        off_p, nb_p = off_t.ctypes.data, nb_t.ctypes.data
+        covers = np.zeros(max(int(vtx[-1]), 1), dtype=np.int32) if want_covers else None
+    sizes = np.zeros(max(G, 1), dtype=np.int32)
+    st = Stats()
+    rc = lib.vc_mvc_batch(G, vtx.ctypes.data, edge.ctypes.data, off_p, nb_p, 1 if on_dev else 0,
+                          ctypes.byref(config) if config else None, _stream(stream), sizes.ctypes.data,
+                          _ptr(covers) if covers is not None else None, ctypes.byref(st))
+    _check(rc, "vc_mvc_batch")
+    return sizes[:G], covers, st.as_dict()
+
+
+def greedy(offsets, neighbors, config: Config | None = None, stream=None):
+    """Greedy upper bound of Sec. II-B computed on the GPU."""
+    lib = load()
+    g, keep = _graph(offsets, neighbors)
+    cover = _cover_buffer(g, offsets)
+    size = ctypes.c_int32(-1)
+    rc = lib.vc_greedy(ctypes.byref(g), ctypes.byref(config) if config else None, _stream(stream), _ptr(cover),
+                       ctypes.byref(size))
+    _check(rc, "vc_greedy")
+    return int(size.value), cover[: g.n]
+
+
+def reduce_node(offsets, neighbors, deg, S: int, m: int, problem: int, bound: int, rules: int = RULE_ALL,
+                config: Config | None = None, stream=None):
+    """One tree node's fixpoint reduction on the GPU (rule tests)."""
+    lib = load()
+    g, keep = _graph(offsets, neighbors)
+    if g.on_device:
+        import torch
+        d = deg.to(dtype=torch.int32).contiguous().clone()
+    else:
+        d = np.array(deg, dtype=np.int32).copy()
+        if d.size == 0:
+            d = np.zeros(1, dtype=np.int32)
+    s = ctypes.c_int32(S)
+    mm = ctypes.c_int32(m)
+    pruned = ctypes.c_int32(0)
+    rc = lib.vc_reduce_node(ctypes.byref(g), _ptr(d), ctypes.byref(s), ctypes.byref(mm), int(problem), int(bound),
+                            int(rules), ctypes.byref(config) if config else None, _stream(stream),
+                            ctypes.byref(pruned))
+    _check(rc, "vc_reduce_node")
+    return d[: g.n], int(s.value), int(mm.value), bool(pruned.value)
+
+
+def last_sm_nodes() -> np.ndarray:
+    """Search-tree nodes expanded per SM by the last traversal (Sec. V-C load measure)."""
+    lib = load()
+    buf = np.zeros(1024, dtype=np.int64)
+    rc = lib.vc_last_sm_nodes(buf.ctypes.data, buf.size)
+    if rc < 0:
+        raise VCError(rc, "vc_last_sm_nodes")
+    return buf[:rc].copy()
+
+
+def release():
+    _check(load().vc_release(), "vc_release")

@@ -1,0 +1,479 @@
+// vc_device.cuh - device building blocks of the traversal: one worker (a thread block of WT
+// threads) holds the current tree node in shared memory and applies the reduction rules, the
+// maximum-degree selection and the two branch removals to it.
+//
+// Shared-memory layout of a worker (all offsets 16-byte aligned):
+//   [entry]  EntryHeader (16 B) + degree array W[n_max] padded to 16 B   <- copied to/from stacks
+//   [marks]  one bit per vertex: chosen for S in the current pass
+//   [list]   int32[n_max]: the vertices chosen in the current pass (each once)
+//   [sc]     kScratchWords int32: pass counters, broadcasts, per-warp reduction keys
+//
+// Degree-array semantics (Sec. IV-B): d[v] >= 0 is v's degree in G - S, d[v] = -1 means v is in S.
+// W is int16_t or int32_t; -1 is the sentinel at both widths.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "vc_internal.h"
+
+namespace vc {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// Scratch word indices.
+enum : int {
+    kScCount = 0,   // entries in the removal list
+    kScEdges = 1,   // edges removed by the current removal
+    kScB0 = 2,      // broadcast slots
+    kScB1 = 3,
+    kScB2 = 4,
+    kScB3 = 5,
+    kScB4 = 6,
+    kScB5 = 7,
+    kScKeys = 32,   // 32 x u64 per-warp argmax keys (words 32..95)
+};
+
+// ------------------------------------------------------------------------------------------------
+// Memory-model helpers (PTX acquire/release at GPU scope)
+// ------------------------------------------------------------------------------------------------
+__device__ __forceinline__ int32_t ld_acquire(const int32_t *p) {
+    int32_t v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ int32_t ld_relaxed(const int32_t *p) {
+    int32_t v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u32(uint32_t *p, uint32_t v) {
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_release(int32_t *p, int32_t v) {
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ uint32_t smid() {
+    uint32_t s;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(s));
+    return s;
+}
+
+// Records the first error of the launch.
+__device__ __forceinline__ void raise_status(Control *ctrl, int32_t code) {
+    atomicCAS(&ctrl->status, VC_OK, code);
+}
+
+// Maximum of 64-bit keys across a warp (two 32-bit warp reductions).
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long k) {
+    uint32_t hi = (uint32_t)(k >> 32), lo = (uint32_t)k;
+    uint32_t mhi = __reduce_max_sync(kFull, hi);
+    uint32_t mlo = __reduce_max_sync(kFull, hi == mhi ? lo : 0u);
+    return ((unsigned long long)mhi << 32) | mlo;
+}
+
+// ------------------------------------------------------------------------------------------------
+// The problem a worker is currently working on (uniform across the block).
+// ------------------------------------------------------------------------------------------------
+struct Ctx {
+    const int32_t *off;  // n+1 offsets of this graph
+    const int32_t *adj;  // its neighbours
+    Problem *prob;
+    int32_t *cover;      // its cover mask (n entries)
+    int32_t n;
+    int32_t kind;
+    int32_t k;
+    int32_t index;
+};
+
+__device__ __forceinline__ Ctx make_ctx(const Params &P, int32_t p) {
+    Ctx c;
+    Problem *pr = P.problems + p;
+    c.off = P.offsets + pr->off_base;
+    c.adj = P.neighbors + pr->adj_base;
+    c.prob = pr;
+    c.cover = P.cover + pr->cover_base;
+    c.n = pr->n;
+    c.kind = pr->kind;
+    c.k = pr->k;
+    c.index = p;
+    return c;
+}
+
+// Per-worker statistics kept in registers by thread 0.
+struct Tally {
+    unsigned long long nodes = 0, pushes = 0, pops = 0, donations = 0, dequeues = 0, passes = 0,
+                       csr = 0, bytes = 0;
+    int32_t max_depth = 0;
+};
+
+// ------------------------------------------------------------------------------------------------
+// Worker
+// ------------------------------------------------------------------------------------------------
+template <typename W, int WT>
+struct Worker {
+    static constexpr int kWarps = WT / 32;
+    EntryHeader *hdr;
+    W *d;
+    uint32_t *marks;
+    int32_t *list;
+    int32_t *sc;
+    unsigned long long *keys;
+    int tid, lane, warp;
+    int32_t entry_bytes;
+
+    __device__ Worker(uint8_t *smem, int32_t n_max) {
+        const int32_t eb = entry_bytes_for(n_max, (int32_t)sizeof(W));
+        hdr = reinterpret_cast<EntryHeader *>(smem);
+        d = reinterpret_cast<W *>(smem + 16);
+        marks = reinterpret_cast<uint32_t *>(smem + eb);
+        list = reinterpret_cast<int32_t *>(smem + eb + pad16(((int64_t)n_max + 31) / 32 * 4));
+        sc = list + pad16((int64_t)n_max * 4) / 4;
+        keys = reinterpret_cast<unsigned long long *>(sc + kScKeys);
+        tid = threadIdx.x;
+        lane = tid & 31;
+        warp = tid >> 5;
+        entry_bytes = eb;
+    }
+
+    __device__ __forceinline__ int deg(int v) const { return (int)d[v]; }
+
+    // Atomic decrement of d[u] in shared memory.  For 16-bit entries the containing 32-bit word
+    // is decremented in the right half; a live vertex with a removed neighbour has degree >= 1, so
+    // the half never borrows from its neighbour.
+    __device__ __forceinline__ void dec(int u) {
+        if constexpr (sizeof(W) == 4) {
+            atomicSub(reinterpret_cast<int *>(d) + u, 1);
+        } else {
+            int *word = reinterpret_cast<int *>(d) + (u >> 1);
+            atomicSub(word, (u & 1) ? 0x10000 : 1);
+        }
+    }
+
+    __device__ __forceinline__ bool marked(int u) const { return (marks[u >> 5] >> (u & 31)) & 1u; }
+
+    // Choose u for S in the current pass (once, however many proposers).
+    __device__ __forceinline__ void propose(int u) {
+        const uint32_t bit = 1u << (u & 31);
+        const uint32_t old = atomicOr(&marks[u >> 5], bit);
+        if (!(old & bit)) list[atomicAdd(&sc[kScCount], 1)] = u;
+    }
+
+    // Clears scratch state; call once per kernel before any pass.
+    __device__ void init_scratch(int32_t n_max) {
+        for (int i = tid; i < (n_max + 31) / 32; i += WT) marks[i] = 0;
+        for (int i = tid; i < kScratchWords; i += WT) sc[i] = 0;
+        __syncthreads();
+    }
+
+    // ---- node loading / storing ---------------------------------------------------------------
+
+    // Root node of a problem (Sec. IV-A: the search starts from the whole graph): degrees from the
+    // CSR, |S| = 0, m = offsets[n] / 2.
+    __device__ void load_root(const Ctx &c) {
+        for (int v = tid; v < c.n; v += WT) d[v] = (W)(__ldg(c.off + v + 1) - __ldg(c.off + v));
+        if (tid == 0) {
+            hdr->problem = c.index;
+            hdr->S = 0;
+            hdr->m = __ldg(c.off + c.n) / 2;
+            hdr->branch = -1;
+        }
+        __syncthreads();
+    }
+
+    // Copies an entry of `bytes` (header + degree array of the entry's graph) from global memory.
+    // Loads go through L2 only (.cg) because the producer may be another SM.
+    __device__ void load_entry(const uint8_t *src, int32_t bytes) {
+        const int4 *s = reinterpret_cast<const int4 *>(src);
+        int4 *t = reinterpret_cast<int4 *>(hdr);
+        for (int i = tid; i < bytes / 16; i += WT) t[i] = __ldcg(s + i);
+        __syncthreads();
+    }
+
+    // Copies the current node to global memory with its header's branch field set to `branch`.
+    __device__ void store_entry(uint8_t *dst, int32_t bytes, int32_t branch) {
+        int4 *t = reinterpret_cast<int4 *>(dst);
+        const int4 *s = reinterpret_cast<const int4 *>(hdr);
+        for (int i = tid; i < bytes / 16; i += WT) {
+            int4 v = s[i];
+            if (i == 0) v.w = branch;
+            __stcg(t + i, v);
+        }
+    }
+
+    // ---- removal (Sec. IV-B) --------------------------------------------------------------------
+
+    // Moves every vertex of the removal list into S: each listed vertex's live neighbours outside
+    // the list lose one degree, m loses every edge with a listed endpoint (an edge between two
+    // listed vertices once), |S| grows by the list length.  One warp per listed vertex, its lanes
+    // splitting the vertex's adjacency list.  Must follow a barrier that ended the proposals.
+    __device__ void apply_list(const Ctx &c, Tally &t) {
+        const int cnt = sc[kScCount];
+        int edges = 0, words = 0;
+        for (int i = warp; i < cnt; i += kWarps) {
+            const int u = list[i];
+            const int b = __ldg(c.off + u), e = __ldg(c.off + u + 1);
+            words += e - b;
+            for (int j = b + lane; j < e; j += 32) {
+                const int x = __ldg(c.adj + j);
+                if (deg(x) == -1) continue;
+                if (marked(x)) {
+                    if (x > u) edges++;
+                } else {
+                    dec(x);
+                    edges++;
+                }
+            }
+        }
+        edges = __reduce_add_sync(kFull, edges);
+        if (lane == 0 && edges) atomicAdd(&sc[kScEdges], edges);
+        if (lane == 0) t.csr += words;
+        __syncthreads();
+        for (int i = tid; i < cnt; i += WT) {
+            const int u = list[i];
+            d[u] = (W)-1;
+            marks[u >> 5] = 0u;
+        }
+        if (tid == 0) {
+            hdr->S += cnt;
+            hdr->m -= sc[kScEdges];
+            sc[kScEdges] = 0;
+            sc[kScCount] = 0;
+        }
+        __syncthreads();
+    }
+
+    // Ends a pass: returns true (and applies the removal) iff some thread proposed a vertex.
+    __device__ __forceinline__ bool finish_pass(const Ctx &c, bool proposed, Tally &t) {
+        if (tid == 0) t.passes++;
+        if (!__syncthreads_or(proposed)) return false;
+        apply_list(c, t);
+        return true;
+    }
+
+    // ---- warp-cooperative adjacency scans --------------------------------------------------------
+
+    // The first `want` (1 or 2) live neighbours of v in id order; the whole warp participates and
+    // every lane gets the answer.  Neighbour lists are sorted, so the first live ones found in
+    // chunk order are the smallest ids.
+    __device__ __forceinline__ void live_neighbours(const Ctx &c, int v, int want, int &a, int &b,
+                                                     int &words) const {
+        a = -1;
+        b = -1;
+        const int lo = __ldg(c.off + v), hi = __ldg(c.off + v + 1);
+        for (int j = lo; j < hi; j += 32) {
+            const bool in = j + lane < hi;
+            const int x = in ? __ldg(c.adj + j + lane) : 0;
+            unsigned live = __ballot_sync(kFull, in && deg(x) != -1);
+            words += min(32, hi - j);
+            while (live) {
+                const int src = __ffs(live) - 1;
+                live &= live - 1;
+                const int y = __shfl_sync(kFull, x, src);
+                if (a < 0) {
+                    a = y;
+                } else {
+                    b = y;
+                    break;
+                }
+            }
+            if (a >= 0 && (want == 1 || b >= 0)) break;
+        }
+    }
+
+    // Whether u and w are adjacent in the input graph: the warp scans the shorter sorted list.
+    __device__ __forceinline__ bool adjacent(const Ctx &c, int u, int w, int &words) const {
+        int lo_u = __ldg(c.off + u), hi_u = __ldg(c.off + u + 1);
+        int lo_w = __ldg(c.off + w), hi_w = __ldg(c.off + w + 1);
+        int lo = lo_u, hi = hi_u, target = w;
+        if (hi_w - lo_w < hi_u - lo_u) {
+            lo = lo_w;
+            hi = hi_w;
+            target = u;
+        }
+        for (int j = lo; j < hi; j += 32) {
+            const bool in = j + lane < hi;
+            const int x = in ? __ldg(c.adj + j + lane) : 0x7fffffff;
+            words += min(32, hi - j);
+            if (__ballot_sync(kFull, x == target)) return true;
+            if (__ballot_sync(kFull, x > target)) return false;
+        }
+        return false;
+    }
+
+    // ---- reduction rules (Sec. II-B; tie-breaks of Sec. IV-D) -----------------------------------
+    // Each pass reads the degree array without changing it while it proposes, then applies all
+    // proposals at once, so the outcome does not depend on thread timing.
+
+    // Degree-one: the live neighbour u of a degree-one vertex v enters S; if u also has degree one
+    // (an isolated edge) only the smaller id of the pair enters.
+    __device__ bool pass_degree_one(const Ctx &c, Tally &t) {
+        bool proposed = false;
+        int words = 0;
+        for (int base = warp * 32; base < c.n; base += WT) {
+            const int v = base + lane;
+            const int dv = v < c.n ? deg(v) : -1;
+            unsigned cand = __ballot_sync(kFull, dv == 1);
+            while (cand) {
+                const int cv = base + __ffs(cand) - 1;
+                cand &= cand - 1;
+                int u, unused;
+                live_neighbours(c, cv, 1, u, unused, words);
+                if (u < 0) continue;  // unreachable for a consistent degree array
+                if (lane == 0 && !(deg(u) == 1 && u > cv)) {
+                    propose(u);
+                    proposed = true;
+                }
+            }
+        }
+        if (lane == 0) t.csr += words;
+        return finish_pass(c, proposed, t);
+    }
+
+    // Degree-two-triangle: if N(v) = {u, w} and uw is an edge, u and w enter S; among degree-two
+    // vertices of one triangle only the smallest id applies the rule.
+    __device__ bool pass_degree_two_triangle(const Ctx &c, Tally &t) {
+        bool proposed = false;
+        int words = 0;
+        for (int base = warp * 32; base < c.n; base += WT) {
+            const int v = base + lane;
+            const int dv = v < c.n ? deg(v) : -1;
+            unsigned cand = __ballot_sync(kFull, dv == 2);
+            while (cand) {
+                const int cv = base + __ffs(cand) - 1;
+                cand &= cand - 1;
+                int u, w;
+                live_neighbours(c, cv, 2, u, w, words);
+                if (u < 0 || w < 0) continue;  // unreachable for a consistent degree array
+                if (!adjacent(c, u, w, words)) continue;
+                if (lane == 0 && !((deg(u) == 2 && u < cv) || (deg(w) == 2 && w < cv))) {
+                    propose(u);
+                    propose(w);
+                    proposed = true;
+                }
+            }
+        }
+        if (lane == 0) t.csr += words;
+        return finish_pass(c, proposed, t);
+    }
+
+    // High-degree: a vertex whose degree exceeds the threshold enters S.  Threshold best-|S|-1
+    // for MVC, k-|S| for PVC (`bound` is best or k).
+    __device__ bool pass_high_degree(const Ctx &c, int32_t bound, Tally &t) {
+        const int thr = (c.kind == kMVC) ? bound - hdr->S - 1 : bound - hdr->S;
+        bool proposed = false;
+        for (int v = tid; v < c.n; v += WT) {
+            const int dv = deg(v);
+            if (dv != -1 && dv > thr) {
+                propose(v);
+                proposed = true;
+            }
+        }
+        return finish_pass(c, proposed, t);
+    }
+
+    // |S| part of the stop check: MVC needs |S| < best, PVC needs |S| <= k.
+    __device__ __forceinline__ bool size_exceeded(const Ctx &c, int32_t bound) const {
+        return (c.kind == kMVC) ? hdr->S >= bound : hdr->S > bound;
+    }
+
+    // Applies the chosen rules until a whole round changes nothing.  With early_exit, returns true
+    // as soon as |S| alone prunes the node (sound: |S| only grows); otherwise runs to the fixpoint.
+    __device__ bool reduce(const Ctx &c, int32_t bound, int rules, bool early_exit, Tally &t) {
+        for (;;) {
+            bool changed = false;
+            if (rules & kRuleDeg1) {
+                if (pass_degree_one(c, t)) {
+                    changed = true;
+                    if (early_exit && size_exceeded(c, bound)) return true;
+                }
+            }
+            if (rules & kRuleDeg2Tri) {
+                if (pass_degree_two_triangle(c, t)) {
+                    changed = true;
+                    if (early_exit && size_exceeded(c, bound)) return true;
+                }
+            }
+            if (rules & kRuleHigh) {
+                if (pass_high_degree(c, bound, t)) {
+                    changed = true;
+                    if (early_exit && size_exceeded(c, bound)) return true;
+                }
+            }
+            if (!changed) return false;
+        }
+    }
+
+    // Stop check (Sec. II-B): prune when |S| is too large or m > t^2 with t = best-|S|-1 (MVC) or
+    // k-|S| (PVC).
+    __device__ __forceinline__ bool must_stop(const Ctx &c, int32_t bound) const {
+        if (size_exceeded(c, bound)) return true;
+        const long long t = (c.kind == kMVC) ? (long long)bound - hdr->S - 1 : (long long)bound - hdr->S;
+        return (long long)hdr->m > t * t;
+    }
+
+    // Maximum-degree live vertex, lowest id on ties (Sec. II-B, IV-B).  Key = (d+1, ~v) so removed
+    // vertices (key 0) never win; returns -1 when no vertex is live.
+    __device__ int argmax(const Ctx &c) {
+        unsigned long long key = 0ull;
+        for (int v = tid; v < c.n; v += WT) {
+            const int dv = deg(v);
+            if (dv >= 0) {
+                const unsigned long long k = ((unsigned long long)(dv + 1) << 32) | (0xffffffffu - (uint32_t)v);
+                key = k > key ? k : key;
+            }
+        }
+        key = warp_max_u64(key);
+        if constexpr (kWarps > 1) {
+            if (lane == 0) keys[warp] = key;
+            __syncthreads();
+            unsigned long long k2 = lane < kWarps ? keys[lane] : 0ull;
+            key = warp_max_u64(k2);
+        }
+        return key == 0ull ? -1 : (int)(0xffffffffu - (uint32_t)key);
+    }
+
+    // Puts the single vertex v into S (the "v" child of Sec. II-B).
+    __device__ void take_vertex(const Ctx &c, int v, Tally &t) {
+        if (tid == 0) propose(v);
+        __syncthreads();
+        apply_list(c, t);
+    }
+
+    // Puts every live neighbour of v into S (the "N(v)" child of Sec. II-B).
+    __device__ void take_neighbourhood(const Ctx &c, int v, Tally &t) {
+        const int lo = __ldg(c.off + v), hi = __ldg(c.off + v + 1);
+        bool proposed = false;
+        for (int j = lo + tid; j < hi; j += WT) {
+            const int x = __ldg(c.adj + j);
+            if (deg(x) != -1) {
+                propose(x);
+                proposed = true;
+            }
+        }
+        if (tid == 0) t.csr += hi - lo;
+        if (__syncthreads_or(proposed)) apply_list(c, t);
+    }
+
+    // Writes the current node's S as a 0/1 mask.
+    __device__ void write_cover(const Ctx &c) {
+        for (int v = tid; v < c.n; v += WT) __stcg(c.cover + v, deg(v) == -1 ? 1 : 0);
+    }
+};
+
+}  // namespace vc

@@ -1,0 +1,133 @@
+// vc_internal.h - layouts shared by the host side and the kernels of libvc.
+//
+// One launch solves one or more independent problems (graphs).  A problem is MVC or PVC(k).
+// Device memory of a launch (all owned by the library's cached workspace):
+//
+//   CSR          packed offsets / neighbours of every problem (read-only, one copy, Sec. IV-B)
+//   Problem[G]   per-problem constants and mutable search state (best, found flag, work units)
+//   Control      launch-wide status word, termination counter, worklist tickets, statistics
+//   cover        Σ n_g int32 0/1 masks: the best cover found so far per problem
+//   stacks       workers x depth x entry_bytes: one local stack per worker (Sec. IV-A, IV-E)
+//   worklist     capacity x entry_bytes slots + capacity sequence words (Sec. IV-A, IV-C)
+//
+// An entry (stack or worklist) is a 16-byte header followed by the degree array of the problem,
+// padded to a multiple of 16 bytes:
+//   header { problem index, |S|, m, pending branch vertex }
+// The pending branch vertex makes the entry a lazily built child: an entry with branch = v >= 0
+// stands for its degree array with every live neighbour of v moved into S (the "N(v)" child of
+// Sec. II-B); the worker that takes the entry applies that removal first.  branch = -1 means the
+// degree array is the node itself.
+#pragma once
+
+#include <stdint.h>
+
+#include "../../include/vc.h"
+
+namespace vc {
+
+enum ProblemKind : int32_t { kMVC = 0, kPVC = 1 };
+enum RuleBits : int32_t { kRuleDeg1 = 1, kRuleDeg2Tri = 2, kRuleHigh = 4, kRuleAll = 7 };
+
+struct alignas(16) EntryHeader {
+    int32_t problem;  // index into the Problem table
+    int32_t S;        // |S|
+    int32_t m;        // edges of G - S
+    int32_t branch;   // pending N(branch) removal, or -1
+};
+
+struct alignas(16) Problem {
+    // constants, written by the host
+    int64_t off_base;    // first offset of this graph in the packed offsets array
+    int64_t adj_base;    // first neighbour of this graph in the packed neighbour array
+    int64_t cover_base;  // first entry of this graph's cover mask
+    int32_t n;           // vertices
+    int32_t m;           // edges
+    int32_t kind;        // kMVC or kPVC
+    int32_t k;           // PVC parameter
+    // search state, written by the kernels
+    int32_t best;        // MVC: size of the best cover found so far (greedy bound first)
+    int32_t found;       // PVC: 1 once a cover of size <= k was found
+    int32_t cover_size;  // size of the cover currently held in the cover mask
+    int32_t lock;        // cover-capture lock (0 free, 1 held)
+    int32_t greedy;      // greedy upper bound
+    int32_t units;       // work units alive: unclaimed root + worklist entries + workers holding work
+    int32_t done;        // 1 once the last unit was released
+    int32_t pad;
+};
+
+struct alignas(16) Control {
+    int32_t status;       // VC_OK, or the first error code raised by any worker
+    int32_t units_total;  // Σ units over problems; 0 means the whole launch is finished
+    int32_t next_root;    // next problem whose root node has not been claimed
+    int32_t num_problems;
+    uint32_t wl_head;     // worklist consumer ticket
+    uint32_t wl_tail;     // worklist producer ticket
+    int32_t max_depth;
+    int32_t pad0;
+    unsigned long long nodes;
+    unsigned long long stack_pushes;
+    unsigned long long stack_pops;
+    unsigned long long donations;
+    unsigned long long worklist_pops;
+    unsigned long long rule_passes;
+    unsigned long long csr_words;
+    unsigned long long entry_bytes;
+};
+
+// Kernel arguments (passed by value).
+struct Params {
+    const int32_t *offsets;
+    const int32_t *neighbors;
+    Problem *problems;
+    int32_t num_problems;
+    int32_t n_max;           // largest n of the launch (sizes the degree-array buffers)
+    int32_t entry_bytes;     // 16 + degree-array bytes padded to 16
+    int32_t stack_depth;     // entries per local stack
+    Control *ctrl;
+    int32_t *cover;          // Σ n cover masks
+    uint8_t *stacks;         // workers x stack_depth x entry_bytes
+    uint8_t *wl_slots;       // wl_capacity x entry_bytes
+    uint32_t *wl_seq;        // wl_capacity sequence words
+    int32_t wl_capacity;
+    int32_t wl_threshold;    // donate while (tail - head) < threshold
+    int64_t idle_timeout_ns;
+    const volatile int32_t *cancel;
+    unsigned long long *sm_nodes;  // per-SM node counters
+};
+
+// Debug single-node reduction arguments.
+struct ReduceParams {
+    const int32_t *offsets;
+    const int32_t *neighbors;
+    int32_t n;
+    int32_t problem;  // kMVC / kPVC
+    int32_t bound;    // best (MVC) or k (PVC)
+    int32_t rules;
+    int32_t *deg;     // n entries, in/out (device)
+    int32_t *io;      // [0] = S, [1] = m, [2] = pruned (out)
+};
+
+#ifdef __CUDACC__
+#define VC_HD __host__ __device__
+#else
+#define VC_HD
+#endif
+
+// Shared-memory bytes one worker needs for a launch whose largest graph has n_max vertices.
+VC_HD inline int32_t pad16(int64_t b) { return (int32_t)((b + 15) & ~int64_t(15)); }
+VC_HD inline int32_t entry_bytes_for(int32_t n_max, int32_t width_bytes) {
+    return 16 + pad16((int64_t)n_max * width_bytes);
+}
+// Scratch words after the entry: marks bitmask, removal list, counters and reduction slots.
+constexpr int kScratchWords = 96;
+// Per-SM node counters are indexed by %smid modulo this power of two.
+constexpr int kSmSlots = 1024;
+VC_HD inline int32_t smem_bytes_for(int32_t n_max, int32_t width_bytes) {
+    int64_t b = entry_bytes_for(n_max, width_bytes);
+    b += pad16(((int64_t)n_max + 31) / 32 * 4);  // marks
+    b += pad16((int64_t)n_max * 4);             // removal list
+    b += kScratchWords * 4;
+    return (int32_t)b;
+}
+
+}  // namespace vc

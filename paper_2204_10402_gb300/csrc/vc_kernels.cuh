@@ -1,0 +1,426 @@
+// vc_kernels.cuh - kernels of libvc (templated on degree-array width W and worker size WT).
+//
+//   validate_kernel     checks the CSR rules of vc.h (one thread per vertex)
+//   greedy_kernel       greedy upper bound per problem (Sec. II-B): seeds best, the cover and the
+//                       problem's work unit
+//   traverse_kernel     persistent hybrid traversal (Sec. IV-A): local stack + device worklist
+//                       with termination (Sec. IV-C), rules (Sec. IV-D), branch (Sec. IV-B)
+//   reduce_node_kernel  one node's fixpoint reduction (rule tests)
+//
+// Every wait is bounded by %globaltimer: an idle worker that finds no work for idle_timeout_ns,
+// or a cover-lock wait that lasts as long, records VC_ETIMEOUT and returns.
+#pragma once
+
+#include "vc_device.cuh"
+
+namespace vc {
+
+// ------------------------------------------------------------------------------------------------
+// CSR validation: offsets monotone from 0, neighbours in range, sorted strictly ascending, no
+// self-loops, every edge listed at both endpoints, offsets[n] equal to the expected length.
+// ------------------------------------------------------------------------------------------------
+__global__ void validate_kernel(const int32_t *offsets, const int32_t *neighbors, const Problem *probs,
+                                const int64_t *adj_len, int32_t num_problems, int64_t total_vertices,
+                                Control *ctrl);
+
+__global__ void init_worklist_kernel(uint32_t *seq, int32_t capacity);
+
+// ------------------------------------------------------------------------------------------------
+// Greedy upper bound (Sec. II-B; the oracle's reading R5): one worker per problem.
+// ------------------------------------------------------------------------------------------------
+template <typename W, int WT>
+__global__ void __launch_bounds__(WT) greedy_kernel(Params P) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    Worker<W, WT> w(smem, P.n_max);
+    w.init_scratch(P.n_max);
+    Tally t;
+    if (w.tid == 0) w.sc[kScB0] = ld_relaxed(&P.ctrl->status);
+    __syncthreads();
+    if (w.sc[kScB0] != VC_OK) return;
+    for (int p = blockIdx.x; p < P.num_problems; p += gridDim.x) {
+        const Ctx c = make_ctx(P, p);
+        if (c.n == 0) {
+            if (w.tid == 0) {
+                c.prob->greedy = c.prob->cover_size = c.prob->best = 0;
+                c.prob->m = 0;
+                if (c.kind == kPVC && c.k >= 0) c.prob->found = 1;
+                c.prob->units = 0;
+                c.prob->done = 1;
+            }
+            continue;
+        }
+        w.load_root(c);
+        const int32_t m0 = w.hdr->m;
+        for (;;) {
+            w.reduce(c, 0, kRuleDeg1 | kRuleDeg2Tri, false, t);
+            if (w.hdr->m == 0) break;
+            const int v = w.argmax(c);
+            if (v < 0) break;  // unreachable: m > 0 implies a live vertex of degree >= 1
+            w.take_vertex(c, v, t);
+        }
+        w.write_cover(c);
+        __threadfence();
+        __syncthreads();
+        if (w.tid == 0) {
+            Problem *pr = c.prob;
+            const int32_t S = w.hdr->S;
+            pr->m = m0;
+            pr->greedy = S;
+            pr->best = S;
+            pr->cover_size = S;
+            bool search;
+            if (c.kind == kMVC) {
+                search = S > 0;  // an edgeless graph needs no search
+            } else {
+                if (c.k >= 0 && S <= c.k) pr->found = 1;  // greedy already fits (reading R6)
+                search = c.k >= 0 && S > c.k;
+            }
+            pr->units = search ? 1 : 0;
+            pr->done = search ? 0 : 1;
+            if (search) atomicAdd(&P.ctrl->units_total, 1);
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Worklist (Sec. IV-A, IV-C): a bounded ring of entry slots with one sequence word per slot.
+// Slot s is free for producer ticket q when seq[s] == q and holds the entry of ticket q when
+// seq[s] == q + 1; the consumer frees it for the next lap with seq[s] = q + capacity.  Neither
+// side ever waits inside an operation: a full ring sends the child to the local stack, an empty
+// ring returns to the idle loop.  The capacity is a power of two.
+// ------------------------------------------------------------------------------------------------
+__device__ __forceinline__ long long wl_reserve(const Params &P) {
+    const uint32_t mask = (uint32_t)P.wl_capacity - 1u;
+    uint32_t pos = ld_relaxed_u32(&P.ctrl->wl_tail);
+    for (int tries = 0; tries < 32; ++tries) {
+        const uint32_t seq = ld_acquire_u32(&P.wl_seq[pos & mask]);
+        const int32_t dif = (int32_t)(seq - pos);
+        if (dif == 0) {
+            const uint32_t prev = atomicCAS(&P.ctrl->wl_tail, pos, pos + 1u);
+            if (prev == pos) return (long long)pos;
+            pos = prev;
+        } else if (dif < 0) {
+            return -1;  // full
+        } else {
+            pos = ld_relaxed_u32(&P.ctrl->wl_tail);
+        }
+    }
+    return -1;
+}
+
+__device__ __forceinline__ long long wl_take(const Params &P) {
+    const uint32_t mask = (uint32_t)P.wl_capacity - 1u;
+    uint32_t pos = ld_relaxed_u32(&P.ctrl->wl_head);
+    for (int tries = 0; tries < 32; ++tries) {
+        const uint32_t seq = ld_acquire_u32(&P.wl_seq[pos & mask]);
+        const int32_t dif = (int32_t)(seq - (pos + 1u));
+        if (dif == 0) {
+            const uint32_t prev = atomicCAS(&P.ctrl->wl_head, pos, pos + 1u);
+            if (prev == pos) return (long long)pos;
+            pos = prev;
+        } else if (dif < 0) {
+            return -1;  // empty, or its producer is still writing
+        } else {
+            pos = ld_relaxed_u32(&P.ctrl->wl_head);
+        }
+    }
+    return -1;
+}
+
+// Gives back the work unit a worker held for problem p (its node and local stack are finished).
+__device__ __forceinline__ void release_unit(const Params &P, int32_t p) {
+    Problem *pr = P.problems + p;
+    __threadfence();
+    if (atomicSub(&pr->units, 1) == 1) st_release(&pr->done, 1);
+    atomicSub(&P.ctrl->units_total, 1);
+}
+
+__device__ __forceinline__ bool cover_lock(const Params &P, Problem *pr) {
+    const uint64_t t0 = globaltimer_ns();
+    while (atomicCAS(&pr->lock, 0, 1) != 0) {
+        if (globaltimer_ns() - t0 > (uint64_t)P.idle_timeout_ns) {
+            raise_status(P.ctrl, VC_ETIMEOUT);
+            return false;
+        }
+        __nanosleep(64);
+    }
+    __threadfence();
+    return true;
+}
+
+// An edgeless node passed the stop check: MVC lowers best (atomicMin) and, if it still holds the
+// smallest size under the cover lock, writes its cover; PVC raises the found flag and the first
+// worker to raise it writes the cover (Sec. IV-A).
+template <typename W, int WT>
+__device__ void record_solution(const Params &P, Worker<W, WT> &w, const Ctx &c) {
+    const int32_t S = w.hdr->S;
+    bool locked = false, write = false;
+    if (w.tid == 0) {
+        if (c.kind == kMVC) {
+            const int32_t old = atomicMin(&c.prob->best, S);
+            if (S < old) {
+                locked = cover_lock(P, c.prob);
+                write = locked && S < ld_relaxed(&c.prob->cover_size);
+            }
+        } else {
+            write = atomicCAS(&c.prob->found, 0, 1) == 0;
+        }
+        w.sc[kScB3] = write;
+    }
+    __syncthreads();
+    if (w.sc[kScB3]) {
+        w.write_cover(c);
+        __threadfence();
+    }
+    __syncthreads();
+    if (w.tid == 0) {
+        if (write) {
+            st_release(&c.prob->cover_size, S);
+            __threadfence();
+        }
+        if (locked) atomicExch(&c.prob->lock, 0);
+    }
+}
+
+// Finds the next node for a worker whose local stack is empty: an unclaimed root first, then the
+// worklist; idles with a growing sleep while other workers still hold work.  Returns 0 (stop),
+// 1 (a root is loaded) or 2 (a worklist entry is loaded).  Sec. IV-C: the search is over when
+// the worklist is empty and no worker holds work, i.e. when no work unit is left.
+template <typename W, int WT>
+__device__ int acquire(const Params &P, Worker<W, WT> &w, Tally &t) {
+    Control *ctrl = P.ctrl;
+    if (w.tid == 0) {
+        int result = 0, arg = 0;
+        while (ld_relaxed(&ctrl->next_root) < P.num_problems) {
+            const int r = atomicAdd(&ctrl->next_root, 1);
+            if (r >= P.num_problems) break;
+            if (ld_relaxed(&P.problems[r].units) > 0) {
+                result = 1;
+                arg = r;
+                break;
+            }
+        }
+        if (!result) {
+            uint64_t t0 = 0;
+            unsigned sleep_ns = 32;
+            for (;;) {
+                if (ld_relaxed(&ctrl->status) != VC_OK) break;
+                const long long pos = wl_take(P);
+                if (pos >= 0) {
+                    result = 2;
+                    arg = (int)(uint32_t)pos;
+                    break;
+                }
+                if (ld_acquire(&ctrl->units_total) == 0) break;
+                if (P.cancel && *P.cancel) {
+                    raise_status(ctrl, VC_ECANCELLED);
+                    break;
+                }
+                const uint64_t now = globaltimer_ns();
+                if (t0 == 0) {
+                    t0 = now;
+                } else if (now - t0 > (uint64_t)P.idle_timeout_ns) {
+                    raise_status(ctrl, VC_ETIMEOUT);
+                    break;
+                }
+                __nanosleep(sleep_ns);
+                if (sleep_ns < 512) sleep_ns *= 2;
+            }
+        }
+        w.sc[kScB4] = result;
+        w.sc[kScB5] = arg;
+    }
+    __syncthreads();
+    const int result = w.sc[kScB4];
+    const int arg = w.sc[kScB5];
+    if (result == 1) {
+        w.load_root(make_ctx(P, arg));
+    } else if (result == 2) {
+        const uint32_t pos = (uint32_t)arg;
+        const uint32_t slot = pos & ((uint32_t)P.wl_capacity - 1u);
+        w.load_entry(P.wl_slots + (size_t)slot * P.entry_bytes, P.entry_bytes);
+        if (w.tid == 0) {
+            st_release_u32(&P.wl_seq[slot], pos + (uint32_t)P.wl_capacity);
+            t.dequeues++;
+            t.bytes += P.entry_bytes;
+        }
+    }
+    return result;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Persistent hybrid traversal (Sec. IV-A): one worker per thread block.
+// ------------------------------------------------------------------------------------------------
+template <typename W, int WT>
+__global__ void __launch_bounds__(WT) traverse_kernel(Params P) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    Worker<W, WT> w(smem, P.n_max);
+    w.init_scratch(P.n_max);
+    Tally t;
+    Control *ctrl = P.ctrl;
+    const int32_t eb = P.entry_bytes;
+    uint8_t *stack = P.stacks + (size_t)blockIdx.x * (size_t)P.stack_depth * (size_t)eb;
+    const uint32_t wl_mask = (uint32_t)P.wl_capacity - 1u;
+    int top = 0;
+    int cur = -1;
+    bool stop = false;
+    Ctx c;
+    c.n = 0;
+
+    if (w.tid == 0) w.sc[kScB0] = ld_relaxed(&ctrl->status);
+    __syncthreads();
+    if (w.sc[kScB0] != VC_OK) return;
+
+    while (!stop) {
+        // ---- acquire: local stack first (Sec. IV-A), then a root or the worklist ----
+        if (top > 0) {
+            --top;
+            w.load_entry(stack + (size_t)top * eb, eb);
+            if (w.tid == 0) {
+                t.pops++;
+                t.bytes += eb;
+            }
+        } else {
+            if (cur >= 0 && w.tid == 0) release_unit(P, cur);
+            cur = -1;
+            const int got = acquire(P, w, t);
+            if (got == 0) break;
+            cur = w.hdr->problem;
+            c = make_ctx(P, cur);
+        }
+        if (w.hdr->branch >= 0) {  // a lazily stored N(v) child: apply the removal now
+            w.take_neighbourhood(c, w.hdr->branch, t);
+            if (w.tid == 0) w.hdr->branch = -1;
+        }
+
+        // ---- expand nodes, continuing into the "v" child after each branch ----
+        for (;;) {
+            if (w.tid == 0) {
+                t.nodes++;
+                w.sc[kScB0] = (c.kind == kMVC) ? ld_relaxed(&c.prob->best) : c.k;
+                w.sc[kScB1] = (c.kind == kPVC) ? ld_relaxed(&c.prob->found) : 0;
+                w.sc[kScB2] = ld_relaxed(&ctrl->status);
+            }
+            __syncthreads();
+            const int32_t bound = w.sc[kScB0];  // one snapshot of best per node (reading R3)
+            if (w.sc[kScB2] != VC_OK) {
+                stop = true;
+                break;
+            }
+            if (w.sc[kScB1]) {  // PVC already answered: drop this problem's remaining work
+                top = 0;
+                break;
+            }
+            if (w.size_exceeded(c, bound)) break;
+            if (w.reduce(c, bound, kRuleAll, true, t)) break;
+            if (w.must_stop(c, bound)) break;
+            if (w.hdr->m == 0) {
+                record_solution(P, w, c);
+                break;
+            }
+            const int v = w.argmax(c);
+            if (v < 0) {  // unreachable: m > 0 implies a live vertex of degree >= 1
+                if (w.tid == 0) raise_status(ctrl, VC_EINVAL);
+                stop = true;
+                break;
+            }
+            const int dv = w.deg(v);
+            const int32_t S = w.hdr->S;
+            // The N(v) child puts dv vertices into S; skip it when that alone prunes it.
+            const bool keep = (c.kind == kMVC) ? (S + dv < bound) : (S + dv <= c.k);
+            if (keep) {
+                if (w.tid == 0) {
+                    long long pos = -1;
+                    const uint32_t tail = ld_relaxed_u32(&ctrl->wl_tail);
+                    const uint32_t head = ld_relaxed_u32(&ctrl->wl_head);
+                    if ((int32_t)(tail - head) < P.wl_threshold) pos = wl_reserve(P);
+                    w.sc[kScB3] = pos >= 0;
+                    w.sc[kScB4] = (int32_t)(uint32_t)(pos >= 0 ? pos : 0);
+                }
+                __syncthreads();
+                if (w.sc[kScB3]) {  // donate (Sec. IV-A: the worklist is below its threshold)
+                    const uint32_t pos = (uint32_t)w.sc[kScB4];
+                    w.store_entry(P.wl_slots + (size_t)(pos & wl_mask) * eb, eb, v);
+                    __threadfence();
+                    __syncthreads();
+                    if (w.tid == 0) {
+                        atomicAdd(&c.prob->units, 1);
+                        atomicAdd(&ctrl->units_total, 1);
+                        st_release_u32(&P.wl_seq[pos & wl_mask], pos + 1u);
+                        t.donations++;
+                        t.bytes += eb;
+                    }
+                } else {  // push on the local stack
+                    if (top >= P.stack_depth) {
+                        if (w.tid == 0) raise_status(ctrl, VC_ESTACK);
+                        stop = true;
+                        break;
+                    }
+                    w.store_entry(stack + (size_t)top * eb, eb, v);
+                    ++top;
+                    if (w.tid == 0) {
+                        t.pushes++;
+                        t.bytes += eb;
+                        t.max_depth = top > t.max_depth ? top : t.max_depth;
+                    }
+                    __syncthreads();
+                }
+            }
+            w.take_vertex(c, v, t);
+        }
+    }
+
+    // ---- statistics ----
+    if (w.lane == 0 && t.csr) atomicAdd(&ctrl->csr_words, t.csr);
+    if (w.tid == 0) {
+        atomicAdd(&ctrl->nodes, t.nodes);
+        atomicAdd(&ctrl->stack_pushes, t.pushes);
+        atomicAdd(&ctrl->stack_pops, t.pops);
+        atomicAdd(&ctrl->donations, t.donations);
+        atomicAdd(&ctrl->worklist_pops, t.dequeues);
+        atomicAdd(&ctrl->rule_passes, t.passes);
+        atomicAdd(&ctrl->entry_bytes, t.bytes);
+        atomicMax(&ctrl->max_depth, t.max_depth);
+        if (P.sm_nodes) atomicAdd(&P.sm_nodes[smid() & (kSmSlots - 1)], t.nodes);
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// One node's reduction (tests): reads an int32 degree array, reduces it to the fixpoint in shared
+// memory (no early exit, like the oracle), writes it back with |S|, m and the stop verdict.
+// ------------------------------------------------------------------------------------------------
+template <typename W, int WT>
+__global__ void __launch_bounds__(WT) reduce_node_kernel(ReduceParams R) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    Worker<W, WT> w(smem, R.n);
+    w.init_scratch(R.n);
+    Tally t;
+    Ctx c;
+    c.off = R.offsets;
+    c.adj = R.neighbors;
+    c.prob = nullptr;
+    c.cover = nullptr;
+    c.n = R.n;
+    c.kind = R.problem;
+    c.k = R.bound;
+    c.index = 0;
+    for (int v = w.tid; v < R.n; v += WT) w.d[v] = (W)R.deg[v];
+    if (w.tid == 0) {
+        w.hdr->problem = 0;
+        w.hdr->S = R.io[0];
+        w.hdr->m = R.io[1];
+        w.hdr->branch = -1;
+    }
+    __syncthreads();
+    w.reduce(c, R.bound, R.rules, false, t);
+    const bool pruned = w.must_stop(c, R.bound);
+    for (int v = w.tid; v < R.n; v += WT) R.deg[v] = w.deg(v);
+    if (w.tid == 0) {
+        R.io[0] = w.hdr->S;
+        R.io[1] = w.hdr->m;
+        R.io[2] = pruned ? 1 : 0;
+    }
+}
+
+}  // namespace vc

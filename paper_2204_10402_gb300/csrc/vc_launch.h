@@ -1,0 +1,28 @@
+// vc_launch.h - host-side entry points into the templated kernels, one set per degree-array
+// width (instantiated in vc_kern_w16.cu and vc_kern_w32.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "vc_internal.h"
+
+namespace vc {
+
+struct Launchers {
+    int (*greedy)(int wt, int grid, int smem, cudaStream_t s, const Params &P);
+    int (*traverse)(int wt, int grid, int smem, cudaStream_t s, const Params &P);
+    int (*reduce)(int wt, int smem, cudaStream_t s, const ReduceParams &R);
+    // Resident blocks per SM of the traversal kernel at this worker size and shared memory.
+    int (*occupancy)(int wt, int smem, int *blocks_per_sm);
+};
+
+const Launchers &launchers_w16();
+const Launchers &launchers_w32();
+
+// Non-templated kernels (vc_common.cu).
+int launch_validate(const int32_t *offsets, const int32_t *neighbors, const Problem *probs,
+                    const int64_t *adj_len, int32_t num_problems, int64_t total_vertices, Control *ctrl,
+                    cudaStream_t s);
+int launch_init_worklist(uint32_t *seq, int32_t capacity, cudaStream_t s);
+
+}  // namespace vc

@@ -1,0 +1,65 @@
+// vc_launch_impl.cuh - instantiates the kernels of one degree-array width W for every supported
+// worker size and exposes them through a Launchers table.
+#pragma once
+
+#include "vc_kernels.cuh"
+#include "vc_launch.h"
+
+namespace vc {
+
+template <typename Kernel>
+static int prepare(Kernel k, int smem) {
+    if (smem > 48 * 1024) {
+        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+            return VC_ECUDA;
+    }
+    return VC_OK;
+}
+
+static inline int launch_status() { return cudaPeekAtLastError() == cudaSuccess ? VC_OK : VC_ECUDA; }
+
+#define VC_WT_SWITCH(wt, ...)                               \
+    switch (wt) {                                           \
+        case 32: { constexpr int WT = 32; __VA_ARGS__; } break;   \
+        case 64: { constexpr int WT = 64; __VA_ARGS__; } break;   \
+        case 128: { constexpr int WT = 128; __VA_ARGS__; } break; \
+        case 256: { constexpr int WT = 256; __VA_ARGS__; } break; \
+        case 512: { constexpr int WT = 512; __VA_ARGS__; } break; \
+        default: return VC_EINVAL;                          \
+    }
+
+template <typename W>
+struct LaunchImpl {
+    static int greedy(int wt, int grid, int smem, cudaStream_t s, const Params &P) {
+        VC_WT_SWITCH(wt, {
+            if (int rc = prepare(greedy_kernel<W, WT>, smem)) return rc;
+            greedy_kernel<W, WT><<<grid, WT, smem, s>>>(P);
+        });
+        return launch_status();
+    }
+    static int traverse(int wt, int grid, int smem, cudaStream_t s, const Params &P) {
+        VC_WT_SWITCH(wt, {
+            if (int rc = prepare(traverse_kernel<W, WT>, smem)) return rc;
+            traverse_kernel<W, WT><<<grid, WT, smem, s>>>(P);
+        });
+        return launch_status();
+    }
+    static int reduce(int wt, int smem, cudaStream_t s, const ReduceParams &R) {
+        VC_WT_SWITCH(wt, {
+            if (int rc = prepare(reduce_node_kernel<W, WT>, smem)) return rc;
+            reduce_node_kernel<W, WT><<<1, WT, smem, s>>>(R);
+        });
+        return launch_status();
+    }
+    static int occupancy(int wt, int smem, int *blocks) {
+        VC_WT_SWITCH(wt, {
+            if (int rc = prepare(traverse_kernel<W, WT>, smem)) return rc;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, traverse_kernel<W, WT>, WT, smem) !=
+                cudaSuccess)
+                return VC_ECUDA;
+        });
+        return VC_OK;
+    }
+};
+
+}  // namespace vc

@@ -1,0 +1,260 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+All answers are integers and must match exactly: MVC size, PVC yes/no, the greedy bound, and the
+reduced degree array of a single node (the rule passes are deterministic rounds, Sec. IV-D
+tie-breaks).  Every cover the GPU returns must verify edge by edge and have the reported size.
+Node counts are not compared (the parallel search order differs from the oracle's).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2204_10402_gb300 import graphs as G
+from tests import pins
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def vc():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_2204_10402_gb300 as vc
+    from paper_2204_10402_gb300 import build
+    build.build()
+    vc.load()
+    return vc
+
+
+def small_graphs(count, seed0, n_lo=4, n_hi=40):
+    out = []
+    for i in range(count):
+        u = G.uniform01(seed0 + i, 2)
+        n = n_lo + int(u[0] * (n_hi - n_lo + 1))
+        p = [0.05, 0.1, 0.2, 0.3, 0.5, 0.8][i % 6]
+        out.append(G.gnp(n, p, seed0 + i, draw_offset=2))
+    return out
+
+
+def check_cover(g, cover, size):
+    c = np.asarray(cover).astype(bool)[: g.n]
+    assert c.sum() == size
+    assert oracle.verify_cover(g, c)
+
+
+# ------------------------------------------------------------------------------------------------
+# single-node reduction: bit-exact degree arrays
+# ------------------------------------------------------------------------------------------------
+
+def test_rule_golden_cases(vc):
+    for case in pins.load_rule_cases():
+        g = G.csr_from_edges(case["n"], [e[0] for e in case["edges"]], [e[1] for e in case["edges"]])
+        deg = case.get("start_deg", g.degrees().tolist())
+        for width in (16, 32):
+            cfg = vc.make_config(width=width)
+            d, S, m, pruned = vc.reduce_node(g.offsets, g.neighbors, deg, case.get("start_S", 0),
+                                             case.get("start_m", g.m), case["mode"], case["bound"],
+                                             case["rules"], config=cfg)
+            got = (d.tolist(), S, m, int(pruned))
+            want = (case["expect_deg"], case["expect_S"], case["expect_m"], case["expect_pruned"])
+            assert got == want, (case["name"], width, got, want)
+
+
+@pytest.mark.parametrize("wt", [32, 64, 256])
+def test_reduce_node_random_states(vc, wt):
+    rng_graphs = small_graphs(40, 20000, 10, 150)
+    for i, g in enumerate(rng_graphs):
+        # a random intermediate state: remove a seeded subset, then reduce from there
+        u = G.uniform01(30000 + i, g.n)
+        removed = u < 0.15
+        deg = g.degrees().astype(np.int64)
+        src, dst = g.edges()
+        m = 0
+        for a, b in zip(src.tolist(), dst.tolist()):
+            if removed[a] or removed[b]:
+                if not removed[a]:
+                    deg[a] -= 1
+                if not removed[b]:
+                    deg[b] -= 1
+            else:
+                m += 1
+        deg[removed] = -1
+        S = int(removed.sum())
+        for problem, bound in ((oracle.MVC, S + 6 + i % 9), (oracle.PVC, S + 4 + i % 7)):
+            for rules in (1, 2, 4, 7):
+                want = oracle.reduce_node(g, deg, S, m, problem, bound, rules)
+                got = vc.reduce_node(g.offsets, g.neighbors, deg, S, m, problem, bound, rules,
+                                     config=vc.make_config(worker_threads=wt))
+                assert got[0].tolist() == want[0].tolist(), (i, problem, rules)
+                assert got[1:] == want[1:], (i, problem, rules, got[1:], want[1:])
+
+
+# ------------------------------------------------------------------------------------------------
+# greedy bound: same deterministic rounds and tie-breaks, so identical values
+# ------------------------------------------------------------------------------------------------
+
+def test_greedy_matches_oracle(vc):
+    for g in small_graphs(30, 40000, 5, 200) + [G.gnp(60, 0.1, 0), G.chung_lu(2000, 6.0, 0)]:
+        want, _ = oracle.greedy(g)
+        got, cover = vc.greedy(g.offsets, g.neighbors)
+        assert got == want
+        check_cover(g, cover, got)
+
+
+# ------------------------------------------------------------------------------------------------
+# MVC / PVC answers
+# ------------------------------------------------------------------------------------------------
+
+def test_mvc_closed_forms(vc):
+    cases = [(G.path(n), n // 2) for n in (2, 3, 7, 20)] + [(G.cycle(n), (n + 1) // 2) for n in (3, 4, 9, 31)]
+    cases += [(G.complete(n), n - 1) for n in (2, 5, 12)] + [(G.complete_bipartite(4, 9), 4), (G.star(7), 1),
+                                                          (G.petersen(), 6)]
+    for g, want in cases:
+        a = vc.mvc(g.offsets, g.neighbors)
+        assert a.value == want
+        check_cover(g, a.cover, want)
+
+
+def test_mvc_random_small(vc):
+    for g in small_graphs(60, 50000, 4, 60):
+        want, _, _ = oracle.mvc(g)
+        a = vc.mvc(g.offsets, g.neighbors)
+        assert a.value == want, (g.n, g.m)
+        check_cover(g, a.cover, want)
+
+
+def test_pvc_around_minimum(vc):
+    for g in small_graphs(30, 60000, 6, 60):
+        best, _, _ = oracle.mvc(g)
+        for k in (best - 1, best, best + 1):
+            a = vc.pvc(g.offsets, g.neighbors, k)
+            assert bool(a.value) == (k >= best), (g.n, g.m, k, best)
+            if a.value:
+                assert a.cover_size <= k
+                check_cover(g, a.cover, a.cover_size)
+
+
+@pytest.mark.parametrize("width,wt", [(16, 32), (32, 32), (16, 128), (32, 64), (16, 512)])
+def test_variants_agree(vc, width, wt):
+    for g in small_graphs(12, 70000, 30, 90):
+        want, _, _ = oracle.mvc(g)
+        a = vc.mvc(g.offsets, g.neighbors, config=vc.make_config(width=width, worker_threads=wt))
+        assert a.value == want
+        check_cover(g, a.cover, want)
+
+
+@pytest.mark.parametrize("cfg", [
+    dict(donate_threshold=-1.0),                    # never donate: all-local-stack path
+    dict(worklist_capacity=1, donate_threshold=1.0),
+    dict(donate_threshold=1.0),                     # donate whenever the ring has room
+    dict(num_workers=1),                            # one worker
+    dict(num_workers=3, worklist_capacity=2),
+])
+def test_worklist_stress(vc, cfg):
+    for g in small_graphs(10, 80000, 40, 100):
+        want, _, _ = oracle.mvc(g)
+        a = vc.mvc(g.offsets, g.neighbors, config=vc.make_config(**cfg))
+        assert a.value == want
+        check_cover(g, a.cover, want)
+
+
+def test_device_tensor_inputs(vc):
+    import torch
+    for g in small_graphs(8, 90000, 20, 80):
+        want, _, _ = oracle.mvc(g)
+        off = torch.from_numpy(g.offsets).cuda()
+        nbr = torch.from_numpy(g.neighbors).cuda()
+        a = vc.mvc(off, nbr)
+        assert a.value == want
+        assert a.cover.is_cuda
+        check_cover(g, a.cover.cpu().numpy(), want)
+        p = vc.pvc(off, nbr, want - 1)
+        assert p.value == 0
+
+
+def test_edge_cases(vc):
+    empty = G.csr_from_edges(0, [], [])
+    assert vc.mvc(empty.offsets, empty.neighbors).value == 0
+    iso = G.csr_from_edges(9, [], [])
+    a = vc.mvc(iso.offsets, iso.neighbors)
+    assert a.value == 0 and a.cover.sum() == 0
+    assert vc.pvc(iso.offsets, iso.neighbors, 0).value == 1
+    g = G.petersen()
+    assert vc.pvc(g.offsets, g.neighbors, -1).value == 0
+    assert vc.pvc(g.offsets, g.neighbors, g.n + 5).value == 1
+    one = G.path(2)
+    assert vc.mvc(one.offsets, one.neighbors).value == 1
+
+
+def test_invalid_csr_rejected(vc):
+    g = G.cycle(6)
+    bad = g.neighbors.copy()
+    bad[0] = 5 if bad[0] != 5 else 4    # breaks symmetry / order
+    with pytest.raises(vc.VCError) as e:
+        vc.mvc(g.offsets, bad)
+    assert e.value.code == vc.VC_EINVAL
+    loop = G.csr_from_edges(3, [0, 1], [1, 2])
+    nb = loop.neighbors.copy()
+    nb[0] = 0                            # self-loop
+    with pytest.raises(vc.VCError):
+        vc.mvc(loop.offsets, nb)
+    off = g.offsets.copy()
+    off[2] = off[3] + 1                  # offsets not monotone
+    with pytest.raises(vc.VCError):
+        vc.mvc(off, g.neighbors)
+    # the library stays usable after a rejected call
+    assert vc.mvc(g.offsets, g.neighbors).value == 3
+
+
+def test_idle_timeout_reports_status(vc):
+    # A tiny idle limit makes idle workers give up while one worker still searches: the call must
+    # return VC_ETIMEOUT (not hang, not fault) and the next call must work normally.
+    g = G.gnp(110, 0.12, 123)
+    with pytest.raises(vc.VCError) as e:
+        vc.mvc(g.offsets, g.neighbors, config=vc.make_config(idle_timeout_ns=1, donate_threshold=-1.0))
+    assert e.value.code == vc.VC_ETIMEOUT
+    want, _, _ = oracle.mvc(g)
+    assert vc.mvc(g.offsets, g.neighbors).value == want
+
+
+# ------------------------------------------------------------------------------------------------
+# the benchmark workloads
+# ------------------------------------------------------------------------------------------------
+
+def test_config_gnp60(vc):
+    g = G.gnp(60, 0.10, 0)
+    want, _, _ = oracle.mvc(g)
+    a = vc.mvc(g.offsets, g.neighbors)
+    assert a.value == want
+    check_cover(g, a.cover, want)
+
+
+def test_config_chung_lu_2000_pvc(vc):
+    g = G.chung_lu(2000, 6.0, 0)
+    best, _, _ = oracle.mvc(g)
+    yes = vc.pvc(g.offsets, g.neighbors, best)
+    no = vc.pvc(g.offsets, g.neighbors, best - 1)
+    assert yes.value == 1 and no.value == 0
+    check_cover(g, yes.cover, yes.cover_size)
+    m = vc.mvc(g.offsets, g.neighbors)
+    assert m.value == best
+
+
+@pytest.mark.parametrize("n", [120, 160])
+@pytest.mark.parametrize("width", [16, 32])
+def test_config_planted_clique_family(vc, n, width):
+    g, _ = G.gnp_with_planted_clique(n, 0.05, round(25 * n / 400), 0)
+    want, _, _ = oracle.mvc(g)
+    a = vc.mvc(g.offsets, g.neighbors, config=vc.make_config(width=width))
+    assert a.value == want
+    check_cover(g, a.cover, want)
+
+
+def test_batch_matches_oracle(vc):
+    b = G.batch_gnp(256)
+    sizes, covers, st = vc.mvc_batch(b.vtx, b.edge, b.offsets, b.neighbors)
+    for i, g in enumerate(b.graphs):
+        want, _, _ = oracle.mvc(g)
+        assert sizes[i] == want, i
+        check_cover(g, covers[b.vtx[i]: b.vtx[i + 1]], want)
+    assert st["nodes_visited"] > 0
