@@ -70,9 +70,10 @@ typedef struct {
     int32_t width;              /* degree-array entry width in bits: 16 or 32 */
     int32_t worklist_capacity;  /* worklist entries */
     float donate_threshold;     /* donate while the worklist holds fewer than this fraction of its capacity */
-    int64_t idle_timeout_ns;    /* an idle worker that finds no work for this long aborts with VC_ETIMEOUT (default 20 s) */
+    int64_t idle_timeout_ns;    /* VC_ETIMEOUT once an idle worker saw no progress anywhere for this long (default 20 s) */
     int32_t skip_validation;    /* 1: trust the CSR and skip the device check */
-    int32_t max_stack_bytes;    /* unused, reserved (0) */
+    int32_t stage_csr;          /* 1: copy each worker's current graph CSR into shared memory when it fits
+                                   (fewer resident workers, shared-memory latency); 0: read it through L1 */
     const volatile int32_t *cancel;  /* optional host-mapped or device flag; nonzero aborts with VC_ECANCELLED */
 } vc_config;
 
@@ -91,6 +92,7 @@ typedef struct {
     int32_t workers;            /* persistent workers launched */
     int32_t worker_threads;     /* threads per worker */
     int32_t width;              /* 16 or 32 */
+    int32_t csr_staged;         /* 1 if the workers read the CSR from shared memory */
     int32_t status;             /* device status word (VC_OK or an error code) */
     float kernel_ms;            /* traversal kernel time (CUDA events on the call's stream) */
     float total_ms;             /* whole call (validation, greedy, traversal, copies) */

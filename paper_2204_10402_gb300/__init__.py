@@ -45,7 +45,7 @@ class Config(ctypes.Structure):
     _fields_ = [("worker_threads", ctypes.c_int32), ("num_workers", ctypes.c_int32),
                 ("width", ctypes.c_int32), ("worklist_capacity", ctypes.c_int32),
                 ("donate_threshold", ctypes.c_float), ("idle_timeout_ns", ctypes.c_int64),
-                ("skip_validation", ctypes.c_int32), ("max_stack_bytes", ctypes.c_int32),
+                ("skip_validation", ctypes.c_int32), ("stage_csr", ctypes.c_int32),
                 ("cancel", ctypes.c_void_p)]
 
 
@@ -55,7 +55,8 @@ class Stats(ctypes.Structure):
                 ("worklist_pops", ctypes.c_int64), ("rule_passes", ctypes.c_int64),
                 ("csr_words", ctypes.c_int64), ("entry_bytes_moved", ctypes.c_int64),
                 ("max_depth", ctypes.c_int32), ("greedy_ub", ctypes.c_int32), ("workers", ctypes.c_int32),
-                ("worker_threads", ctypes.c_int32), ("width", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("worker_threads", ctypes.c_int32), ("width", ctypes.c_int32), ("csr_staged", ctypes.c_int32),
+                ("status", ctypes.c_int32),
                 ("kernel_ms", ctypes.c_float), ("total_ms", ctypes.c_float)]
 
     def as_dict(self) -> dict:

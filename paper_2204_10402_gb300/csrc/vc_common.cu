@@ -53,9 +53,10 @@ __global__ void validate_kernel(const int32_t *offsets, const int32_t *neighbors
     }
 }
 
-__global__ void init_worklist_kernel(uint32_t *seq, int32_t capacity) {
+__global__ void init_worklist_kernel(uint32_t *seq, int32_t capacity, Control *ctrl) {
     const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < capacity) seq[i] = (uint32_t)i;
+    if (i == 0) ctrl->wl_space = capacity;
 }
 
 int launch_validate(const int32_t *offsets, const int32_t *neighbors, const Problem *probs,
@@ -70,8 +71,8 @@ int launch_validate(const int32_t *offsets, const int32_t *neighbors, const Prob
     return cudaPeekAtLastError() == cudaSuccess ? VC_OK : VC_ECUDA;
 }
 
-int launch_init_worklist(uint32_t *seq, int32_t capacity, cudaStream_t s) {
-    init_worklist_kernel<<<(capacity + 255) / 256, 256, 0, s>>>(seq, capacity);
+int launch_init_worklist(uint32_t *seq, int32_t capacity, Control *ctrl, cudaStream_t s) {
+    init_worklist_kernel<<<(capacity + 255) / 256, 256, 0, s>>>(seq, capacity, ctrl);
     return cudaPeekAtLastError() == cudaSuccess ? VC_OK : VC_ECUDA;
 }
 

@@ -7,6 +7,8 @@
 //   [marks]  one bit per vertex: chosen for S in the current pass
 //   [list]   int32[n_max]: the vertices chosen in the current pass (each once)
 //   [sc]     kScratchWords int32: pass counters, broadcasts, per-warp reduction keys
+//   [csr]    optional copy of the current graph's CSR (offsets, then neighbours), so that the
+//            adjacency walks of the rules and branches cost shared-memory latency
 //
 // Degree-array semantics (Sec. IV-B): d[v] >= 0 is v's degree in G - S, d[v] = -1 means v is in S.
 // W is int16_t or int32_t; -1 is the sentinel at both widths.
@@ -91,7 +93,7 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long k)
 // The problem a worker is currently working on (uniform across the block).
 // ------------------------------------------------------------------------------------------------
 struct Ctx {
-    const int32_t *off;  // n+1 offsets of this graph
+    const int32_t *off;  // n+1 offsets of this graph (global, or the worker's shared-memory copy)
     const int32_t *adj;  // its neighbours
     Problem *prob;
     int32_t *cover;      // its cover mask (n entries)
@@ -134,10 +136,13 @@ struct Worker {
     int32_t *list;
     int32_t *sc;
     unsigned long long *keys;
+    int32_t *csr;
     int tid, lane, warp;
     int32_t entry_bytes;
+    int32_t csr_words;
+    int32_t staged;  // problem whose CSR is in csr, or -1
 
-    __device__ Worker(uint8_t *smem, int32_t n_max) {
+    __device__ Worker(uint8_t *smem, int32_t n_max, int32_t csr_capacity = 0) {
         const int32_t eb = entry_bytes_for(n_max, (int32_t)sizeof(W));
         hdr = reinterpret_cast<EntryHeader *>(smem);
         d = reinterpret_cast<W *>(smem + 16);
@@ -145,6 +150,9 @@ struct Worker {
         list = reinterpret_cast<int32_t *>(smem + eb + pad16(((int64_t)n_max + 31) / 32 * 4));
         sc = list + pad16((int64_t)n_max * 4) / 4;
         keys = reinterpret_cast<unsigned long long *>(sc + kScKeys);
+        csr = sc + kScratchWords;
+        csr_words = csr_capacity;
+        staged = -1;
         tid = threadIdx.x;
         lane = tid & 31;
         warp = tid >> 5;
@@ -181,16 +189,34 @@ struct Worker {
         __syncthreads();
     }
 
+    // Points c at a shared-memory copy of its graph's CSR (copied when the problem changes), if the
+    // launch reserved room for it and the graph fits.
+    __device__ void stage(Ctx &c) {
+        if (csr_words == 0) return;
+        const int n1 = c.n + 1;
+        if (c.index != staged) {
+            const int len = c.off[c.n];
+            if (n1 + len > csr_words) return;  // does not fit: keep reading global memory
+            __syncthreads();                    // nobody still reads the previous copy
+            for (int i = tid; i < n1; i += WT) csr[i] = c.off[i];
+            for (int i = tid; i < len; i += WT) csr[n1 + i] = c.adj[i];
+            staged = c.index;
+            __syncthreads();
+        }
+        c.off = csr;
+        c.adj = csr + n1;
+    }
+
     // ---- node loading / storing ---------------------------------------------------------------
 
     // Root node of a problem (Sec. IV-A: the search starts from the whole graph): degrees from the
     // CSR, |S| = 0, m = offsets[n] / 2.
     __device__ void load_root(const Ctx &c) {
-        for (int v = tid; v < c.n; v += WT) d[v] = (W)(__ldg(c.off + v + 1) - __ldg(c.off + v));
+        for (int v = tid; v < c.n; v += WT) d[v] = (W)(c.off[v + 1] - c.off[v]);
         if (tid == 0) {
             hdr->problem = c.index;
             hdr->S = 0;
-            hdr->m = __ldg(c.off + c.n) / 2;
+            hdr->m = c.off[c.n] / 2;
             hdr->branch = -1;
         }
         __syncthreads();
@@ -227,10 +253,10 @@ struct Worker {
         int edges = 0, words = 0;
         for (int i = warp; i < cnt; i += kWarps) {
             const int u = list[i];
-            const int b = __ldg(c.off + u), e = __ldg(c.off + u + 1);
+            const int b = c.off[u], e = c.off[u + 1];
             words += e - b;
             for (int j = b + lane; j < e; j += 32) {
-                const int x = __ldg(c.adj + j);
+                const int x = c.adj[j];
                 if (deg(x) == -1) continue;
                 if (marked(x)) {
                     if (x > u) edges++;
@@ -275,10 +301,10 @@ struct Worker {
                                                      int &words) const {
         a = -1;
         b = -1;
-        const int lo = __ldg(c.off + v), hi = __ldg(c.off + v + 1);
+        const int lo = c.off[v], hi = c.off[v + 1];
         for (int j = lo; j < hi; j += 32) {
             const bool in = j + lane < hi;
-            const int x = in ? __ldg(c.adj + j + lane) : 0;
+            const int x = in ? c.adj[j + lane] : 0;
             unsigned live = __ballot_sync(kFull, in && deg(x) != -1);
             words += min(32, hi - j);
             while (live) {
@@ -298,8 +324,8 @@ struct Worker {
 
     // Whether u and w are adjacent in the input graph: the warp scans the shorter sorted list.
     __device__ __forceinline__ bool adjacent(const Ctx &c, int u, int w, int &words) const {
-        int lo_u = __ldg(c.off + u), hi_u = __ldg(c.off + u + 1);
-        int lo_w = __ldg(c.off + w), hi_w = __ldg(c.off + w + 1);
+        int lo_u = c.off[u], hi_u = c.off[u + 1];
+        int lo_w = c.off[w], hi_w = c.off[w + 1];
         int lo = lo_u, hi = hi_u, target = w;
         if (hi_w - lo_w < hi_u - lo_u) {
             lo = lo_w;
@@ -308,7 +334,7 @@ struct Worker {
         }
         for (int j = lo; j < hi; j += 32) {
             const bool in = j + lane < hi;
-            const int x = in ? __ldg(c.adj + j + lane) : 0x7fffffff;
+            const int x = in ? c.adj[j + lane] : 0x7fffffff;
             words += min(32, hi - j);
             if (__ballot_sync(kFull, x == target)) return true;
             if (__ballot_sync(kFull, x > target)) return false;
@@ -457,10 +483,10 @@ struct Worker {
 
     // Puts every live neighbour of v into S (the "N(v)" child of Sec. II-B).
     __device__ void take_neighbourhood(const Ctx &c, int v, Tally &t) {
-        const int lo = __ldg(c.off + v), hi = __ldg(c.off + v + 1);
+        const int lo = c.off[v], hi = c.off[v + 1];
         bool proposed = false;
         for (int j = lo + tid; j < hi; j += WT) {
-            const int x = __ldg(c.adj + j);
+            const int x = c.adj[j];
             if (deg(x) != -1) {
                 propose(x);
                 proposed = true;

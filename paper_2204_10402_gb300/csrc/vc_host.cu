@@ -157,6 +157,7 @@ struct Result {
     Control ctrl;
     float kernel_ms = 0.f;
     int workers = 0, wt = 0, width = 0;
+    bool csr_staged = false;
 };
 
 Problem make_problem(int64_t off_base, int64_t adj_base, int64_t cover_base, int32_t n, int32_t kind, int32_t k) {
@@ -190,7 +191,22 @@ int run(Workspace &ws, const Spec &spec, const vc_config *cfg_in, cudaStream_t s
     const int wbytes = width / 8;
     int wt = cfg.worker_threads ? cfg.worker_threads : default_worker_threads(n_max);
     if (!is_pow2(wt) || wt < 32 || wt > 512) return VC_EINVAL;
-    const int smem = smem_bytes_for(n_max, wbytes);
+    // CSR staging in shared memory: when every graph's CSR size is known and small enough, each
+    // worker keeps a copy of its current graph's CSR next to the degree array.
+    int64_t csr_need = 0;
+    bool known = true;
+    for (size_t i = 0; i < spec.probs.size(); ++i) {
+        if (spec.adj_len[i] < 0) known = false;
+        else csr_need = std::max<int64_t>(csr_need, (int64_t)spec.probs[i].n + 1 + spec.adj_len[i]);
+    }
+    int32_t csr_words = 0;
+    if (known && cfg.stage_csr > 0 && csr_need > 0 && csr_need * 4 <= (int64_t)ws.smem_optin)
+        csr_words = (int32_t)csr_need;
+    int smem = smem_bytes_for(n_max, wbytes, csr_words);
+    if (smem > ws.smem_optin && csr_words) {
+        csr_words = 0;
+        smem = smem_bytes_for(n_max, wbytes, 0);
+    }
     if (smem > ws.smem_optin) return VC_EINVAL;  // graph too large for a shared-memory degree array
     const Launchers &L = width == 16 ? launchers_w16() : launchers_w32();
     int per_sm = 0;
@@ -257,6 +273,7 @@ int run(Workspace &ws, const Spec &spec, const vc_config *cfg_in, cudaStream_t s
     P.cover = static_cast<int32_t *>(ws.cover.p);
     P.wl_capacity = cap;
     P.wl_threshold = threshold;
+    P.csr_words = csr_words;
     P.idle_timeout_ns = cfg.idle_timeout_ns > 0 ? cfg.idle_timeout_ns : kDefaultIdleTimeoutNs;
     P.cancel = cfg.cancel;
     P.sm_nodes = static_cast<unsigned long long *>(ws.sm_nodes.p);
@@ -286,7 +303,7 @@ int run(Workspace &ws, const Spec &spec, const vc_config *cfg_in, cudaStream_t s
         P.stacks = static_cast<uint8_t *>(ws.stacks.p);
         P.wl_slots = static_cast<uint8_t *>(ws.wl_slots.p);
         P.wl_seq = static_cast<uint32_t *>(ws.wl_seq.p);
-        VC_RC(launch_init_worklist(P.wl_seq, cap, s));
+        VC_RC(launch_init_worklist(P.wl_seq, cap, d_ctrl, s));
         VC_CK(cudaMemsetAsync(P.sm_nodes, 0, sizeof(unsigned long long) * (size_t)kSmSlots, s));
         VC_CK(cudaEventRecord(ws.ev0, s));
         VC_RC(L.traverse(wt, workers, smem, s, P));
@@ -316,6 +333,7 @@ int run(Workspace &ws, const Spec &spec, const vc_config *cfg_in, cudaStream_t s
     res.workers = workers;
     res.wt = wt;
     res.width = width;
+    res.csr_staged = csr_words > 0;
     return h_ctrl->status;
 }
 
@@ -335,6 +353,7 @@ void fill_stats(vc_stats *st, const Result &r, double total_ms, int32_t greedy) 
     st->workers = r.workers;
     st->worker_threads = r.wt;
     st->width = r.width;
+    st->csr_staged = r.csr_staged ? 1 : 0;
     st->status = r.ctrl.status;
     st->kernel_ms = r.kernel_ms;
     st->total_ms = (float)total_ms;

@@ -55,13 +55,18 @@ struct alignas(16) Problem {
     int32_t pad;
 };
 
-struct alignas(16) Control {
-    int32_t status;       // VC_OK, or the first error code raised by any worker
-    int32_t units_total;  // Σ units over problems; 0 means the whole launch is finished
-    int32_t next_root;    // next problem whose root node has not been claimed
+// Launch-wide control block.  Words that many workers hit with atomics or polls each own a
+// 128-byte line, so traffic on one never queues behind traffic on another.
+struct alignas(128) Control {
+    alignas(128) int32_t wl_count;     // published worklist entries no consumer has reserved yet
+    alignas(128) int32_t wl_space;     // free worklist slots (initialised to the capacity)
+    alignas(128) uint32_t wl_head;     // consumer tickets
+    alignas(128) uint32_t wl_tail;     // producer tickets
+    alignas(128) int32_t units_total;  // Σ units over problems; 0 means the whole launch is finished
+    alignas(128) uint32_t heartbeat;   // bumped by busy workers; idle workers time out only while it stands still
+    alignas(128) int32_t next_root;    // next problem whose root node has not been claimed
+    alignas(128) int32_t status;       // VC_OK, or the first error code raised by any worker
     int32_t num_problems;
-    uint32_t wl_head;     // worklist consumer ticket
-    uint32_t wl_tail;     // worklist producer ticket
     int32_t max_depth;
     int32_t pad0;
     unsigned long long nodes;
@@ -89,7 +94,8 @@ struct Params {
     uint8_t *wl_slots;       // wl_capacity x entry_bytes
     uint32_t *wl_seq;        // wl_capacity sequence words
     int32_t wl_capacity;
-    int32_t wl_threshold;    // donate while (tail - head) < threshold
+    int32_t wl_threshold;    // donate while fewer than this many entries wait in the worklist
+    int32_t csr_words;       // shared-memory CSR staging capacity in int32 words (0 = read the CSR from global)
     int64_t idle_timeout_ns;
     const volatile int32_t *cancel;
     unsigned long long *sm_nodes;  // per-SM node counters
@@ -118,15 +124,17 @@ VC_HD inline int32_t pad16(int64_t b) { return (int32_t)((b + 15) & ~int64_t(15)
 VC_HD inline int32_t entry_bytes_for(int32_t n_max, int32_t width_bytes) {
     return 16 + pad16((int64_t)n_max * width_bytes);
 }
-// Scratch words after the entry: marks bitmask, removal list, counters and reduction slots.
+// Scratch words after the entry: marks bitmask, removal list, counters and reduction slots, then
+// an optional copy of the current graph's CSR (offsets followed by neighbours).
 constexpr int kScratchWords = 96;
 // Per-SM node counters are indexed by %smid modulo this power of two.
 constexpr int kSmSlots = 1024;
-VC_HD inline int32_t smem_bytes_for(int32_t n_max, int32_t width_bytes) {
+VC_HD inline int32_t smem_bytes_for(int32_t n_max, int32_t width_bytes, int32_t csr_words = 0) {
     int64_t b = entry_bytes_for(n_max, width_bytes);
     b += pad16(((int64_t)n_max + 31) / 32 * 4);  // marks
     b += pad16((int64_t)n_max * 4);             // removal list
     b += kScratchWords * 4;
+    b += pad16((int64_t)csr_words * 4);         // staged CSR
     return (int32_t)b;
 }
 

@@ -23,7 +23,7 @@ __global__ void validate_kernel(const int32_t *offsets, const int32_t *neighbors
                                 const int64_t *adj_len, int32_t num_problems, int64_t total_vertices,
                                 Control *ctrl);
 
-__global__ void init_worklist_kernel(uint32_t *seq, int32_t capacity);
+__global__ void init_worklist_kernel(uint32_t *seq, int32_t capacity, Control *ctrl);
 
 // ------------------------------------------------------------------------------------------------
 // Greedy upper bound (Sec. II-B; the oracle's reading R5): one worker per problem.
@@ -31,14 +31,14 @@ __global__ void init_worklist_kernel(uint32_t *seq, int32_t capacity);
 template <typename W, int WT>
 __global__ void __launch_bounds__(WT) greedy_kernel(Params P) {
     extern __shared__ __align__(16) uint8_t smem[];
-    Worker<W, WT> w(smem, P.n_max);
+    Worker<W, WT> w(smem, P.n_max, P.csr_words);
     w.init_scratch(P.n_max);
     Tally t;
     if (w.tid == 0) w.sc[kScB0] = ld_relaxed(&P.ctrl->status);
     __syncthreads();
     if (w.sc[kScB0] != VC_OK) return;
     for (int p = blockIdx.x; p < P.num_problems; p += gridDim.x) {
-        const Ctx c = make_ctx(P, p);
+        Ctx c = make_ctx(P, p);
         if (c.n == 0) {
             if (w.tid == 0) {
                 c.prob->greedy = c.prob->cover_size = c.prob->best = 0;
@@ -49,6 +49,7 @@ __global__ void __launch_bounds__(WT) greedy_kernel(Params P) {
             }
             continue;
         }
+        w.stage(c);
         w.load_root(c);
         const int32_t m0 = w.hdr->m;
         for (;;) {
@@ -84,48 +85,58 @@ __global__ void __launch_bounds__(WT) greedy_kernel(Params P) {
 }
 
 // ------------------------------------------------------------------------------------------------
-// Worklist (Sec. IV-A, IV-C): a bounded ring of entry slots with one sequence word per slot.
-// Slot s is free for producer ticket q when seq[s] == q and holds the entry of ticket q when
-// seq[s] == q + 1; the consumer frees it for the next lap with seq[s] = q + capacity.  Neither
-// side ever waits inside an operation: a full ring sends the child to the local stack, an empty
-// ring returns to the idle loop.  The capacity is a power of two.
+// Worklist (Sec. IV-A, IV-C): a ring of `capacity` entry slots (a power of two) with one sequence
+// word per slot, and four counters on separate lines:
+//   wl_space  free slots            producers reserve one before taking a ticket
+//   wl_tail   producer tickets      ticket t writes slot t mod capacity
+//   wl_count  published entries     consumers reserve one before taking a ticket
+//   wl_head   consumer tickets      ticket t reads slot t mod capacity
+// Slot s is writable for producer ticket t when seq[s] == t and readable for consumer ticket t
+// when seq[s] == t + 1; the consumer frees it for the next lap with seq[s] = t + capacity.
+// A reservation on wl_space / wl_count guarantees that the slot's previous user (or its producer)
+// already holds its ticket, so the only waits are for operations already in progress; they are
+// still bounded by idle_timeout_ns.  An idle poll is one relaxed load of wl_count.
 // ------------------------------------------------------------------------------------------------
-__device__ __forceinline__ long long wl_reserve(const Params &P) {
-    const uint32_t mask = (uint32_t)P.wl_capacity - 1u;
-    uint32_t pos = ld_relaxed_u32(&P.ctrl->wl_tail);
-    for (int tries = 0; tries < 32; ++tries) {
-        const uint32_t seq = ld_acquire_u32(&P.wl_seq[pos & mask]);
-        const int32_t dif = (int32_t)(seq - pos);
-        if (dif == 0) {
-            const uint32_t prev = atomicCAS(&P.ctrl->wl_tail, pos, pos + 1u);
-            if (prev == pos) return (long long)pos;
-            pos = prev;
-        } else if (dif < 0) {
-            return -1;  // full
-        } else {
-            pos = ld_relaxed_u32(&P.ctrl->wl_tail);
+__device__ __forceinline__ bool wait_seq(const Params &P, uint32_t slot, uint32_t want) {
+    uint64_t t0 = 0;
+    while (ld_acquire_u32(&P.wl_seq[slot]) != want) {
+        const uint64_t now = globaltimer_ns();
+        if (t0 == 0) {
+            t0 = now;
+        } else if (now - t0 > (uint64_t)P.idle_timeout_ns) {
+            raise_status(P.ctrl, VC_ETIMEOUT);
+            return false;
         }
+        __nanosleep(20);
     }
-    return -1;
+    return true;
 }
 
-__device__ __forceinline__ long long wl_take(const Params &P) {
-    const uint32_t mask = (uint32_t)P.wl_capacity - 1u;
-    uint32_t pos = ld_relaxed_u32(&P.ctrl->wl_head);
-    for (int tries = 0; tries < 32; ++tries) {
-        const uint32_t seq = ld_acquire_u32(&P.wl_seq[pos & mask]);
-        const int32_t dif = (int32_t)(seq - (pos + 1u));
-        if (dif == 0) {
-            const uint32_t prev = atomicCAS(&P.ctrl->wl_head, pos, pos + 1u);
-            if (prev == pos) return (long long)pos;
-            pos = prev;
-        } else if (dif < 0) {
-            return -1;  // empty, or its producer is still writing
-        } else {
-            pos = ld_relaxed_u32(&P.ctrl->wl_head);
-        }
+// Producer side: a ticket whose slot is ready for writing, or -1 (worklist at its threshold or
+// full: the caller pushes on its local stack instead), or -2 (timed out).
+__device__ __forceinline__ long long wl_reserve(const Params &P) {
+    Control *c = P.ctrl;
+    if (ld_relaxed(&c->wl_count) >= P.wl_threshold) return -1;
+    if (atomicSub(&c->wl_space, 1) <= 0) {
+        atomicAdd(&c->wl_space, 1);
+        return -1;
     }
-    return -1;
+    const uint32_t t = atomicAdd(&c->wl_tail, 1u);
+    if (!wait_seq(P, t & ((uint32_t)P.wl_capacity - 1u), t)) return -2;
+    return (long long)t;
+}
+
+// Consumer side: a ticket whose slot holds a published entry, or -1 (nothing published), or -2.
+__device__ __forceinline__ long long wl_take(const Params &P) {
+    Control *c = P.ctrl;
+    if (ld_relaxed(&c->wl_count) <= 0) return -1;
+    if (atomicSub(&c->wl_count, 1) <= 0) {
+        atomicAdd(&c->wl_count, 1);
+        return -1;
+    }
+    const uint32_t t = atomicAdd(&c->wl_head, 1u);
+    if (!wait_seq(P, t & ((uint32_t)P.wl_capacity - 1u), t + 1u)) return -2;
+    return (long long)t;
 }
 
 // Gives back the work unit a worker held for problem p (its node and local stack are finished).
@@ -202,30 +213,38 @@ __device__ int acquire(const Params &P, Worker<W, WT> &w, Tally &t) {
             }
         }
         if (!result) {
-            uint64_t t0 = 0;
-            unsigned sleep_ns = 32;
+            // The wait ends with work, with the end of the search, or after idle_timeout_ns during
+            // which no busy worker showed progress (heartbeat unchanged): a stalled launch reports
+            // VC_ETIMEOUT instead of spinning forever.  Sleeps grow geometrically (with a per-worker
+            // offset) so that thousands of idle workers do not flood the worklist counters.
+            uint64_t t0 = globaltimer_ns();
+            uint32_t beat = ld_relaxed_u32(&ctrl->heartbeat);
+            unsigned sleep_ns = 64 + (blockIdx.x & 63);
             for (;;) {
-                if (ld_relaxed(&ctrl->status) != VC_OK) break;
                 const long long pos = wl_take(P);
                 if (pos >= 0) {
                     result = 2;
                     arg = (int)(uint32_t)pos;
                     break;
                 }
+                if (pos == -2) break;
+                if (ld_relaxed(&ctrl->status) != VC_OK) break;
                 if (ld_acquire(&ctrl->units_total) == 0) break;
                 if (P.cancel && *P.cancel) {
                     raise_status(ctrl, VC_ECANCELLED);
                     break;
                 }
                 const uint64_t now = globaltimer_ns();
-                if (t0 == 0) {
+                const uint32_t b = ld_relaxed_u32(&ctrl->heartbeat);
+                if (b != beat) {
+                    beat = b;
                     t0 = now;
                 } else if (now - t0 > (uint64_t)P.idle_timeout_ns) {
                     raise_status(ctrl, VC_ETIMEOUT);
                     break;
                 }
                 __nanosleep(sleep_ns);
-                if (sleep_ns < 512) sleep_ns *= 2;
+                if (sleep_ns < 8192) sleep_ns += sleep_ns >> 1;
             }
         }
         w.sc[kScB4] = result;
@@ -242,6 +261,7 @@ __device__ int acquire(const Params &P, Worker<W, WT> &w, Tally &t) {
         w.load_entry(P.wl_slots + (size_t)slot * P.entry_bytes, P.entry_bytes);
         if (w.tid == 0) {
             st_release_u32(&P.wl_seq[slot], pos + (uint32_t)P.wl_capacity);
+            atomicAdd(&ctrl->wl_space, 1);
             t.dequeues++;
             t.bytes += P.entry_bytes;
         }
@@ -255,7 +275,7 @@ __device__ int acquire(const Params &P, Worker<W, WT> &w, Tally &t) {
 template <typename W, int WT>
 __global__ void __launch_bounds__(WT) traverse_kernel(Params P) {
     extern __shared__ __align__(16) uint8_t smem[];
-    Worker<W, WT> w(smem, P.n_max);
+    Worker<W, WT> w(smem, P.n_max, P.csr_words);
     w.init_scratch(P.n_max);
     Tally t;
     Control *ctrl = P.ctrl;
@@ -288,6 +308,7 @@ __global__ void __launch_bounds__(WT) traverse_kernel(Params P) {
             if (got == 0) break;
             cur = w.hdr->problem;
             c = make_ctx(P, cur);
+            w.stage(c);
         }
         if (w.hdr->branch >= 0) {  // a lazily stored N(v) child: apply the removal now
             w.take_neighbourhood(c, w.hdr->branch, t);
@@ -297,7 +318,7 @@ __global__ void __launch_bounds__(WT) traverse_kernel(Params P) {
         // ---- expand nodes, continuing into the "v" child after each branch ----
         for (;;) {
             if (w.tid == 0) {
-                t.nodes++;
+                if ((++t.nodes & 31) == 0) atomicAdd(&ctrl->heartbeat, 1u);
                 w.sc[kScB0] = (c.kind == kMVC) ? ld_relaxed(&c.prob->best) : c.k;
                 w.sc[kScB1] = (c.kind == kPVC) ? ld_relaxed(&c.prob->found) : 0;
                 w.sc[kScB2] = ld_relaxed(&ctrl->status);
@@ -331,10 +352,7 @@ __global__ void __launch_bounds__(WT) traverse_kernel(Params P) {
             const bool keep = (c.kind == kMVC) ? (S + dv < bound) : (S + dv <= c.k);
             if (keep) {
                 if (w.tid == 0) {
-                    long long pos = -1;
-                    const uint32_t tail = ld_relaxed_u32(&ctrl->wl_tail);
-                    const uint32_t head = ld_relaxed_u32(&ctrl->wl_head);
-                    if ((int32_t)(tail - head) < P.wl_threshold) pos = wl_reserve(P);
+                    const long long pos = wl_reserve(P);
                     w.sc[kScB3] = pos >= 0;
                     w.sc[kScB4] = (int32_t)(uint32_t)(pos >= 0 ? pos : 0);
                 }
@@ -348,6 +366,7 @@ __global__ void __launch_bounds__(WT) traverse_kernel(Params P) {
                         atomicAdd(&c.prob->units, 1);
                         atomicAdd(&ctrl->units_total, 1);
                         st_release_u32(&P.wl_seq[pos & wl_mask], pos + 1u);
+                        atomicAdd(&ctrl->wl_count, 1);
                         t.donations++;
                         t.bytes += eb;
                     }

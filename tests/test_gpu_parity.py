@@ -258,3 +258,31 @@ def test_batch_matches_oracle(vc):
         assert sizes[i] == want, i
         check_cover(g, covers[b.vtx[i]: b.vtx[i + 1]], want)
     assert st["nodes_visited"] > 0
+
+
+def load_batch_golden():
+    import os
+    rows = {}
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "batch4096_mvc.txt")
+    for line in open(path):
+        if line.startswith("#"):
+            continue
+        g, n, m, size, nodes = (int(x) for x in line.split())
+        rows[g] = (n, m, size)
+    return rows
+
+
+def test_full_batch_matches_stored_oracle_answers(vc):
+    # The benchmark's launch configuration (defaults, 4096 graphs, device-resident CSR) against the
+    # oracle's answers written by tests/golden/make_batch_golden.py; every cover verifies.
+    import torch
+    b = G.batch_gnp(4096)
+    want = load_batch_golden()
+    off = torch.from_numpy(b.offsets).cuda()
+    nbr = torch.from_numpy(b.neighbors).cuda()
+    sizes, covers, st = vc.mvc_batch(b.vtx, b.edge, off, nbr)
+    covers = covers.cpu().numpy()
+    for i, g in enumerate(b.graphs):
+        assert (g.n, g.m) == want[i][:2]
+        assert sizes[i] == want[i][2], i
+        check_cover(g, covers[b.vtx[i]: b.vtx[i + 1]], want[i][2])
