@@ -140,6 +140,29 @@ int vc_greedy(const vc_graph *g, const vc_config *cfg, void *stream, int32_t *co
 int vc_reduce_node(const vc_graph *g, int32_t *deg, int32_t *S, int32_t *m, int32_t problem,
                    int32_t bound, int32_t rules, const vc_config *cfg, void *stream, int32_t *pruned_out);
 
+/* MVC without any allocation (the paper has no counterpart: this is a deployment variant).
+ * For callers that cannot let a library allocate device memory, e.g. code that runs under a
+ * memory pool or arena owning all device memory, processes that lock their allocator after
+ * start-up, or request paths where cudaMalloc/cudaFree (and the synchronisation they imply) are
+ * not allowed.  The search runs the same kernels as vc_mvc, but all of its scratch lives in one
+ * fixed array of VC_NOALLOC_SCRATCH_BYTES bytes that is part of the library image: every device
+ * that loads the library holds that array until the process exits, and this call allocates
+ * nothing (no cudaMalloc, cudaFree or pinned host memory).
+ *   - g must be on the device (on_device = 1) with n <= VC_NOALLOC_MAX_N; larger graphs and host
+ *     pointers are rejected with VC_EINVAL.  cover_out (n int32, device, may be NULL) and
+ *     *cover_size_out (host) receive the result; cfg and stats may be NULL.
+ *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ *     that device current; make that first call before capturing any stream.
+ *   - All calls share the one array and each call resets what must start from a known value.
+ *     Calls whose GPU work overlaps (other streams, other host threads without ordering) race on
+ *     it; the library serialises calls from one process only on the host side.
+ *   - The call synchronises `stream` twice (after the greedy bound, which sizes the stacks, and at
+ *     the end). */
+#define VC_NOALLOC_MAX_N 512
+#define VC_NOALLOC_SCRATCH_BYTES (32u << 20)
+int vc_mvc_noalloc(const vc_graph *g, const vc_config *cfg, void *stream, int32_t *cover_out,
+                   int32_t *cover_size_out, vc_stats *stats);
+
 /* Per-SM search-tree node counts of the last traversal on the current device (Sec. V-C load
  * measure): counts_out receives min(capacity, SM count) entries; returns the SM count or an
  * error code. */

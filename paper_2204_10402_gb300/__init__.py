@@ -27,7 +27,8 @@ MVC, PVC = 0, 1
 RULE_DEG1, RULE_DEG2TRI, RULE_HIGH, RULE_ALL = 1, 2, 4, 7
 
 EXPORTED = ["vc_mvc", "vc_pvc", "vc_mvc_batch", "vc_greedy", "vc_reduce_node", "vc_last_sm_nodes",
-            "vc_release", "vc_strerror", "vc_version"]
+            "vc_release", "vc_strerror", "vc_version", "vc_mvc_noalloc"]
+NOALLOC_MAX_N = 512
 
 
 class VCError(RuntimeError):
@@ -89,12 +90,13 @@ def load(path: str | None = None):
     lib.vc_greedy.argtypes = [gp, cp, P, P, i32p]
     lib.vc_reduce_node.argtypes = [gp, P, i32p, i32p, i32, i32, i32, cp, P, i32p]
     lib.vc_last_sm_nodes.argtypes = [P, i32]
+    lib.vc_mvc_noalloc.argtypes = [gp, cp, P, P, i32p, sp]
     lib.vc_release.argtypes = []
     lib.vc_strerror.argtypes = [ctypes.c_int]
     lib.vc_strerror.restype = ctypes.c_char_p
     lib.vc_version.argtypes = []
     for name in ("vc_mvc", "vc_pvc", "vc_mvc_batch", "vc_greedy", "vc_reduce_node", "vc_last_sm_nodes",
-                 "vc_release", "vc_version"):
+                 "vc_release", "vc_version", "vc_mvc_noalloc"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -203,6 +205,25 @@ def mvc(offsets, neighbors, config: Config | None = None, stream=None, want_cove
     if cover is not None:
         cover = cover[: g.n]
     return Answer(int(size.value), cover, int(size.value), st.as_dict())
+
+
+def mvc_noalloc(offsets, neighbors, config: Config | None = None, stream=None) -> Answer:
+    """MVC of one small graph (n <= 512) whose CSR is on the device, with no memory allocation by
+    the library: for callers whose device memory is owned by a pool or arena, or whose request
+    path must not call cudaMalloc/cudaFree.  The cover comes back as a device tensor allocated
+    here by torch, outside the library call."""
+    import torch
+    lib = load()
+    g, keep = _graph(offsets, neighbors)
+    if not g.on_device:
+        raise ValueError("mvc_noalloc takes CUDA tensors")
+    cover = torch.empty(max(g.n, 1), dtype=torch.int32, device=offsets.device)
+    size = ctypes.c_int32(-1)
+    st = Stats()
+    rc = lib.vc_mvc_noalloc(ctypes.byref(g), ctypes.byref(config) if config else None, _stream(stream),
+                            cover.data_ptr(), ctypes.byref(size), ctypes.byref(st))
+    _check(rc, "vc_mvc_noalloc")
+    return Answer(int(size.value), cover[: g.n], int(size.value), st.as_dict())
 
 
 def pvc(offsets, neighbors, k: int, config: Config | None = None, stream=None, want_cover: bool = True) -> Answer:
