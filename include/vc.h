@@ -136,9 +136,13 @@ int vc_greedy(const vc_graph *g, const vc_config *cfg, void *stream, int32_t *co
  * (bound = best), 1 = PVC (bound = k).  rules: bit 0 degree-one, bit 1 degree-two-triangle,
  * bit 2 high-degree.  *pruned_out receives 1 iff the stop check prunes the reduced node.
  * Every rule pass is one simultaneous round: vertices that meet the rule at the start of the pass
- * are found, then all of them enter S together. */
+ * are found, then all of them enter S together.
+ * branch = -1 reduces the given state.  branch = v >= 0 (or -2-v) treats the given state as a
+ * fixpoint of the rules, first puts v (or every live neighbour of v) into S, and then reduces the
+ * child the way the traversal does, re-examining only vertices whose degree changed. */
 int vc_reduce_node(const vc_graph *g, int32_t *deg, int32_t *S, int32_t *m, int32_t problem,
-                   int32_t bound, int32_t rules, const vc_config *cfg, void *stream, int32_t *pruned_out);
+                   int32_t bound, int32_t rules, int32_t branch, const vc_config *cfg, void *stream,
+                   int32_t *pruned_out);
 
 /* MVC without any allocation (the paper has no counterpart: this is a deployment variant).
  * For callers that cannot let a library allocate device memory, e.g. code that runs under a

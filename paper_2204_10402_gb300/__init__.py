@@ -88,7 +88,7 @@ def load(path: str | None = None):
     lib.vc_pvc.argtypes = [gp, i32, cp, P, i32p, P, i32p, sp]
     lib.vc_mvc_batch.argtypes = [i32, P, P, P, P, i32, cp, P, P, P, sp]
     lib.vc_greedy.argtypes = [gp, cp, P, P, i32p]
-    lib.vc_reduce_node.argtypes = [gp, P, i32p, i32p, i32, i32, i32, cp, P, i32p]
+    lib.vc_reduce_node.argtypes = [gp, P, i32p, i32p, i32, i32, i32, i32, cp, P, i32p]
     lib.vc_last_sm_nodes.argtypes = [P, i32]
     lib.vc_mvc_noalloc.argtypes = [gp, cp, P, P, i32p, sp]
     lib.vc_release.argtypes = []
@@ -287,8 +287,9 @@ def greedy(offsets, neighbors, config: Config | None = None, stream=None):
 
 
 def reduce_node(offsets, neighbors, deg, S: int, m: int, problem: int, bound: int, rules: int = RULE_ALL,
-                config: Config | None = None, stream=None):
-    """One tree node's fixpoint reduction on the GPU (rule tests)."""
+                config: Config | None = None, stream=None, branch: int = -1):
+    """One tree node's fixpoint reduction on the GPU (rule tests).  branch = v >= 0 (or -2-v) puts v
+    (or N(v)) into S first, treating ``deg`` as a fixpoint, as the traversal does for a child."""
     lib = load()
     g, keep = _graph(offsets, neighbors)
     if g.on_device:
@@ -302,7 +303,7 @@ def reduce_node(offsets, neighbors, deg, S: int, m: int, problem: int, bound: in
     mm = ctypes.c_int32(m)
     pruned = ctypes.c_int32(0)
     rc = lib.vc_reduce_node(ctypes.byref(g), _ptr(d), ctypes.byref(s), ctypes.byref(mm), int(problem), int(bound),
-                            int(rules), ctypes.byref(config) if config else None, _stream(stream),
+                            int(rules), int(branch), ctypes.byref(config) if config else None, _stream(stream),
                             ctypes.byref(pruned))
     _check(rc, "vc_reduce_node")
     return d[: g.n], int(s.value), int(mm.value), bool(pruned.value)

@@ -5,6 +5,8 @@
 // Shared-memory layout of a worker (all offsets 16-byte aligned):
 //   [entry]  EntryHeader (16 B) + degree array W[n_max] padded to 16 B   <- copied to/from stacks
 //   [marks]  one bit per vertex: chosen for S in the current pass
+//   [dirty]  one 64-bit word per 32 vertices: low half = degree changed since the degree-one pass
+//            last looked at the vertex, high half = the same for the degree-two-triangle pass
 //   [list]   int32[n_max]: the vertices chosen in the current pass (each once)
 //   [sc]     kScratchWords int32: pass counters, broadcasts, per-warp reduction keys
 //   [csr]    optional copy of the current graph's CSR (offsets, then neighbours), so that the
@@ -81,6 +83,24 @@ __device__ __forceinline__ void raise_status(Control *ctrl, int32_t code) {
     atomicCAS(&ctrl->status, VC_OK, code);
 }
 
+// Debug builds (-DVC_DEBUG_CHECKS) check indices on the traversal's paths and, instead of making a
+// bad access, record the first failing site and value and raise VC_EINVAL.
+#ifdef VC_DEBUG_CHECKS
+#define VC_CHECK(ctrl, cond, site, value, on_fail)                                  \
+    do {                                                                            \
+        if (!(cond)) {                                                              \
+            if ((ctrl) && atomicCAS(&(ctrl)->dbg_site, 0, (site)) == 0)             \
+                (ctrl)->dbg_value = (int32_t)(value);                               \
+            if (ctrl) raise_status((ctrl), VC_EINVAL);                              \
+            on_fail;                                                                \
+        }                                                                           \
+    } while (0)
+#else
+#define VC_CHECK(ctrl, cond, site, value, on_fail) \
+    do {                                           \
+    } while (0)
+#endif
+
 // Maximum of 64-bit keys across a warp (two 32-bit warp reductions).
 __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long k) {
     uint32_t hi = (uint32_t)(k >> 32), lo = (uint32_t)k;
@@ -117,12 +137,20 @@ __device__ __forceinline__ Ctx make_ctx(const Params &P, int32_t p) {
     return c;
 }
 
-// Per-worker statistics kept in registers by thread 0.
-struct Tally {
-    unsigned long long nodes = 0, pushes = 0, pops = 0, donations = 0, dequeues = 0, passes = 0,
-                       csr = 0, bytes = 0;
-    int32_t max_depth = 0;
+// Per-worker statistics, kept in shared memory (sc words 8..27) so they cost no registers.
+enum TallySlot : int {
+    kTNodes = 0,
+    kTPushes,
+    kTPops,
+    kTDonations,
+    kTDequeues,
+    kTPasses,
+    kTCsr,
+    kTBytes,
+    kTMaxDepth,
+    kTallySlots
 };
+constexpr int kScTally = 8;  // first scratch word of the tally (8-byte aligned)
 
 // ------------------------------------------------------------------------------------------------
 // Worker
@@ -133,26 +161,37 @@ struct Worker {
     EntryHeader *hdr;
     W *d;
     uint32_t *marks;
+    unsigned long long *dirty;
     int32_t *list;
     int32_t *sc;
     unsigned long long *keys;
+    unsigned long long *tally;
     int32_t *csr;
     int tid, lane, warp;
     int32_t entry_bytes;
     int32_t csr_words;
     int32_t staged;  // problem whose CSR is in csr, or -1
+    Control *dbg;    // where debug builds report failed checks (may be null)
+    int32_t cur_n;   // vertices of the current graph (for the debug checks)
+    int32_t n_cap;   // shared-memory capacity in vertices
 
     __device__ Worker(uint8_t *smem, int32_t n_max, int32_t csr_capacity = 0) {
         const int32_t eb = entry_bytes_for(n_max, (int32_t)sizeof(W));
         hdr = reinterpret_cast<EntryHeader *>(smem);
         d = reinterpret_cast<W *>(smem + 16);
         marks = reinterpret_cast<uint32_t *>(smem + eb);
-        list = reinterpret_cast<int32_t *>(smem + eb + pad16(((int64_t)n_max + 31) / 32 * 4));
+        const int32_t mark_bytes = pad16(((int64_t)n_max + 31) / 32 * 4);
+        dirty = reinterpret_cast<unsigned long long *>(smem + eb + mark_bytes);
+        list = reinterpret_cast<int32_t *>(smem + eb + mark_bytes + pad16(((int64_t)n_max + 31) / 32 * 8));
         sc = list + pad16((int64_t)n_max * 4) / 4;
         keys = reinterpret_cast<unsigned long long *>(sc + kScKeys);
+        tally = reinterpret_cast<unsigned long long *>(sc + kScTally);
         csr = sc + kScratchWords;
         csr_words = csr_capacity;
         staged = -1;
+        dbg = nullptr;
+        cur_n = n_max;
+        n_cap = n_max;
         tid = threadIdx.x;
         lane = tid & 31;
         warp = tid >> 5;
@@ -177,14 +216,37 @@ struct Worker {
 
     // Choose u for S in the current pass (once, however many proposers).
     __device__ __forceinline__ void propose(int u) {
+        VC_CHECK(dbg, u >= 0 && u < cur_n, 2, u, return);
         const uint32_t bit = 1u << (u & 31);
         const uint32_t old = atomicOr(&marks[u >> 5], bit);
         if (!(old & bit)) list[atomicAdd(&sc[kScCount], 1)] = u;
     }
 
+    // Dirty tracking.  A degree-one or degree-two-triangle pass only looks at vertices whose degree
+    // changed since that pass last ran, which finds exactly the vertices a full scan would: at the
+    // end of a pass every vertex it looked at that still meets its rule has been dealt with, and a
+    // vertex whose degree did not change since then kept its live neighbourhood (any removed
+    // neighbour lowers the degree), so it still does not meet the rule.  A root, or a state given
+    // from outside, starts with every vertex dirty; a stored node is a fixpoint of the rules and
+    // starts clean, and its pending removal dirties the neighbours of what it removes.
+    __device__ __forceinline__ void touch(int x) { atomicOr(&dirty[x >> 5], 0x100000001ull << (x & 31)); }
+    __device__ void dirty_all(int n) {
+        for (int i = tid; i < (n + 31) / 32; i += WT) {
+            const int rem = n - 32 * i;
+            const unsigned long long m = rem >= 32 ? 0xffffffffull : ((1ull << rem) - 1ull);
+            dirty[i] = m | (m << 32);
+        }
+    }
+    __device__ void dirty_none(int n) {
+        for (int i = tid; i < (n + 31) / 32; i += WT) dirty[i] = 0ull;
+    }
+
     // Clears scratch state; call once per kernel before any pass.
     __device__ void init_scratch(int32_t n_max) {
-        for (int i = tid; i < (n_max + 31) / 32; i += WT) marks[i] = 0;
+        for (int i = tid; i < (n_max + 31) / 32; i += WT) {
+            marks[i] = 0;
+            dirty[i] = 0ull;
+        }
         for (int i = tid; i < kScratchWords; i += WT) sc[i] = 0;
         __syncthreads();
     }
@@ -212,7 +274,9 @@ struct Worker {
     // Root node of a problem (Sec. IV-A: the search starts from the whole graph): degrees from the
     // CSR, |S| = 0, m = offsets[n] / 2.
     __device__ void load_root(const Ctx &c) {
+        __syncthreads();  // no warp still reads the node being replaced
         for (int v = tid; v < c.n; v += WT) d[v] = (W)(c.off[v + 1] - c.off[v]);
+        dirty_all(c.n);
         if (tid == 0) {
             hdr->problem = c.index;
             hdr->S = 0;
@@ -224,10 +288,12 @@ struct Worker {
 
     // Copies an entry of `bytes` (header + degree array of the entry's graph) from global memory.
     // Loads go through L2 only (.cg) because the producer may be another SM.
-    __device__ void load_entry(const uint8_t *src, int32_t bytes) {
+    __device__ void load_entry(const uint8_t *src, int32_t bytes, int32_t n_max) {
+        __syncthreads();  // no warp still reads the node being replaced
         const int4 *s = reinterpret_cast<const int4 *>(src);
         int4 *t = reinterpret_cast<int4 *>(hdr);
         for (int i = tid; i < bytes / 16; i += WT) t[i] = __ldcg(s + i);
+        dirty_none(n_max);
         __syncthreads();
     }
 
@@ -248,30 +314,36 @@ struct Worker {
     // the list lose one degree, m loses every edge with a listed endpoint (an edge between two
     // listed vertices once), |S| grows by the list length.  One warp per listed vertex, its lanes
     // splitting the vertex's adjacency list.  Must follow a barrier that ended the proposals.
-    __device__ void apply_list(const Ctx &c, Tally &t) {
-        const int cnt = sc[kScCount];
+    __device__ void apply_list(const Ctx &c) {
+        int cnt = sc[kScCount];
+        VC_CHECK(dbg, cnt >= 0 && cnt <= c.n, 3, cnt, cnt = 0);
         int edges = 0, words = 0;
         for (int i = warp; i < cnt; i += kWarps) {
             const int u = list[i];
+            VC_CHECK(dbg, u >= 0 && u < c.n, 4, u, continue);
             const int b = c.off[u], e = c.off[u + 1];
+            VC_CHECK(dbg, b >= 0 && e >= b, 15, u, continue);
             words += e - b;
             for (int j = b + lane; j < e; j += 32) {
                 const int x = c.adj[j];
+                VC_CHECK(dbg, x >= 0 && x < c.n, 9, x, continue);
                 if (deg(x) == -1) continue;
                 if (marked(x)) {
                     if (x > u) edges++;
                 } else {
                     dec(x);
+                    touch(x);
                     edges++;
                 }
             }
         }
         edges = __reduce_add_sync(kFull, edges);
         if (lane == 0 && edges) atomicAdd(&sc[kScEdges], edges);
-        if (lane == 0) t.csr += words;
+        if (lane == 0 && words) atomicAdd(&tally[kTCsr], (unsigned long long)words);
         __syncthreads();
         for (int i = tid; i < cnt; i += WT) {
             const int u = list[i];
+            VC_CHECK(dbg, u >= 0 && u < c.n, 16, u, continue);
             d[u] = (W)-1;
             marks[u >> 5] = 0u;
         }
@@ -285,10 +357,10 @@ struct Worker {
     }
 
     // Ends a pass: returns true (and applies the removal) iff some thread proposed a vertex.
-    __device__ __forceinline__ bool finish_pass(const Ctx &c, bool proposed, Tally &t) {
-        if (tid == 0) t.passes++;
+    __device__ __forceinline__ bool finish_pass(const Ctx &c, bool proposed) {
+        if (tid == 0) tally[kTPasses] += 1;
         if (!__syncthreads_or(proposed)) return false;
-        apply_list(c, t);
+        apply_list(c);
         return true;
     }
 
@@ -301,10 +373,13 @@ struct Worker {
                                                      int &words) const {
         a = -1;
         b = -1;
+        VC_CHECK(dbg, v >= 0 && v < c.n, 17, v, return);
         const int lo = c.off[v], hi = c.off[v + 1];
+        VC_CHECK(dbg, lo >= 0 && hi >= lo, 7, v, return);
         for (int j = lo; j < hi; j += 32) {
             const bool in = j + lane < hi;
-            const int x = in ? c.adj[j + lane] : 0;
+            int x = in ? c.adj[j + lane] : 0;
+            VC_CHECK(dbg, x >= 0 && x < c.n, 10, x, x = 0);
             unsigned live = __ballot_sync(kFull, in && deg(x) != -1);
             words += min(32, hi - j);
             while (live) {
@@ -324,6 +399,7 @@ struct Worker {
 
     // Whether u and w are adjacent in the input graph: the warp scans the shorter sorted list.
     __device__ __forceinline__ bool adjacent(const Ctx &c, int u, int w, int &words) const {
+        VC_CHECK(dbg, u >= 0 && u < c.n && w >= 0 && w < c.n, 8, u, return false);
         int lo_u = c.off[u], hi_u = c.off[u + 1];
         int lo_w = c.off[w], hi_w = c.off[w + 1];
         int lo = lo_u, hi = hi_u, target = w;
@@ -348,13 +424,17 @@ struct Worker {
 
     // Degree-one: the live neighbour u of a degree-one vertex v enters S; if u also has degree one
     // (an isolated edge) only the smaller id of the pair enters.
-    __device__ bool pass_degree_one(const Ctx &c, Tally &t) {
+    __device__ bool pass_degree_one(const Ctx &c) {
         bool proposed = false;
         int words = 0;
         for (int base = warp * 32; base < c.n; base += WT) {
+            const unsigned long long dw = dirty[base >> 5];
+            const unsigned bits = (unsigned)dw;
+            if (bits == 0u) continue;
+            if (lane == 0) dirty[base >> 5] = dw & 0xffffffff00000000ull;
             const int v = base + lane;
             const int dv = v < c.n ? deg(v) : -1;
-            unsigned cand = __ballot_sync(kFull, dv == 1);
+            unsigned cand = __ballot_sync(kFull, dv == 1) & bits;
             while (cand) {
                 const int cv = base + __ffs(cand) - 1;
                 cand &= cand - 1;
@@ -367,19 +447,23 @@ struct Worker {
                 }
             }
         }
-        if (lane == 0) t.csr += words;
-        return finish_pass(c, proposed, t);
+        if (lane == 0 && words) atomicAdd(&tally[kTCsr], (unsigned long long)words);
+        return finish_pass(c, proposed);
     }
 
     // Degree-two-triangle: if N(v) = {u, w} and uw is an edge, u and w enter S; among degree-two
     // vertices of one triangle only the smallest id applies the rule.
-    __device__ bool pass_degree_two_triangle(const Ctx &c, Tally &t) {
+    __device__ bool pass_degree_two_triangle(const Ctx &c) {
         bool proposed = false;
         int words = 0;
         for (int base = warp * 32; base < c.n; base += WT) {
+            const unsigned long long dw = dirty[base >> 5];
+            const unsigned bits = (unsigned)(dw >> 32);
+            if (bits == 0u) continue;
+            if (lane == 0) dirty[base >> 5] = dw & 0xffffffffull;
             const int v = base + lane;
             const int dv = v < c.n ? deg(v) : -1;
-            unsigned cand = __ballot_sync(kFull, dv == 2);
+            unsigned cand = __ballot_sync(kFull, dv == 2) & bits;
             while (cand) {
                 const int cv = base + __ffs(cand) - 1;
                 cand &= cand - 1;
@@ -394,13 +478,13 @@ struct Worker {
                 }
             }
         }
-        if (lane == 0) t.csr += words;
-        return finish_pass(c, proposed, t);
+        if (lane == 0 && words) atomicAdd(&tally[kTCsr], (unsigned long long)words);
+        return finish_pass(c, proposed);
     }
 
     // High-degree: a vertex whose degree exceeds the threshold enters S.  Threshold best-|S|-1
     // for MVC, k-|S| for PVC (`bound` is best or k).
-    __device__ bool pass_high_degree(const Ctx &c, int32_t bound, Tally &t) {
+    __device__ bool pass_high_degree(const Ctx &c, int32_t bound) {
         const int thr = (c.kind == kMVC) ? bound - hdr->S - 1 : bound - hdr->S;
         bool proposed = false;
         for (int v = tid; v < c.n; v += WT) {
@@ -410,7 +494,7 @@ struct Worker {
                 proposed = true;
             }
         }
-        return finish_pass(c, proposed, t);
+        return finish_pass(c, proposed);
     }
 
     // |S| part of the stop check: MVC needs |S| < best, PVC needs |S| <= k.
@@ -420,23 +504,23 @@ struct Worker {
 
     // Applies the chosen rules until a whole round changes nothing.  With early_exit, returns true
     // as soon as |S| alone prunes the node (sound: |S| only grows); otherwise runs to the fixpoint.
-    __device__ bool reduce(const Ctx &c, int32_t bound, int rules, bool early_exit, Tally &t) {
+    __device__ bool reduce(const Ctx &c, int32_t bound, int rules, bool early_exit) {
         for (;;) {
             bool changed = false;
             if (rules & kRuleDeg1) {
-                if (pass_degree_one(c, t)) {
+                if (pass_degree_one(c)) {
                     changed = true;
                     if (early_exit && size_exceeded(c, bound)) return true;
                 }
             }
             if (rules & kRuleDeg2Tri) {
-                if (pass_degree_two_triangle(c, t)) {
+                if (pass_degree_two_triangle(c)) {
                     changed = true;
                     if (early_exit && size_exceeded(c, bound)) return true;
                 }
             }
             if (rules & kRuleHigh) {
-                if (pass_high_degree(c, bound, t)) {
+                if (pass_high_degree(c, bound)) {
                     changed = true;
                     if (early_exit && size_exceeded(c, bound)) return true;
                 }
@@ -475,14 +559,16 @@ struct Worker {
     }
 
     // Puts the single vertex v into S (the "v" child of Sec. II-B).
-    __device__ void take_vertex(const Ctx &c, int v, Tally &t) {
+    __device__ void take_vertex(const Ctx &c, int v) {
+        VC_CHECK(dbg, v >= 0 && v < c.n, 5, v, return);
         if (tid == 0) propose(v);
         __syncthreads();
-        apply_list(c, t);
+        apply_list(c);
     }
 
     // Puts every live neighbour of v into S (the "N(v)" child of Sec. II-B).
-    __device__ void take_neighbourhood(const Ctx &c, int v, Tally &t) {
+    __device__ void take_neighbourhood(const Ctx &c, int v) {
+        VC_CHECK(dbg, v >= 0 && v < c.n, 6, v, return);
         const int lo = c.off[v], hi = c.off[v + 1];
         bool proposed = false;
         for (int j = lo + tid; j < hi; j += WT) {
@@ -492,8 +578,8 @@ struct Worker {
                 proposed = true;
             }
         }
-        if (tid == 0) t.csr += hi - lo;
-        if (__syncthreads_or(proposed)) apply_list(c, t);
+        if (tid == 0) atomicAdd(&tally[kTCsr], (unsigned long long)(hi - lo));
+        if (__syncthreads_or(proposed)) apply_list(c);
     }
 
     // Writes the current node's S as a 0/1 mask.

@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <cstdio>
 #include <climits>
 #include <cstring>
 #include <mutex>
@@ -328,6 +329,9 @@ int run(Workspace &ws, const Spec &spec, const vc_config *cfg_in, cudaStream_t s
 
     res.probs.assign(h_probs, h_probs + G);
     res.ctrl = *h_ctrl;
+#ifdef VC_DEBUG_CHECKS
+    if (h_ctrl->dbg_site) fprintf(stderr, "vc debug check failed: site %d value %d\n", h_ctrl->dbg_site, h_ctrl->dbg_value);
+#endif
     res.kernel_ms = 0.f;
     if (spec.search) VC_CK(cudaEventElapsedTime(&res.kernel_ms, ws.ev0, ws.ev1));
     res.workers = workers;
@@ -521,10 +525,11 @@ int vc_greedy(const vc_graph *g, const vc_config *cfg, void *stream, int32_t *co
 }
 
 int vc_reduce_node(const vc_graph *g, int32_t *deg, int32_t *S, int32_t *m, int32_t problem, int32_t bound,
-                   int32_t rules, const vc_config *cfg, void *stream, int32_t *pruned_out) {
+                   int32_t rules, int32_t branch, const vc_config *cfg, void *stream, int32_t *pruned_out) {
     if (check_graph(g) || !deg || !S || !m || !pruned_out || (problem != kMVC && problem != kPVC) ||
         (rules & ~kRuleAll))
         return VC_EINVAL;
+    if (branch >= g->n || (branch <= -2 && -2 - branch >= g->n)) return VC_EINVAL;
     if (g->n == 0) {
         const int64_t t = problem == kMVC ? (int64_t)bound - *S - 1 : (int64_t)bound - *S;
         *pruned_out = (problem == kMVC ? *S >= bound : *S > bound) || (int64_t)*m > t * t;
@@ -589,6 +594,7 @@ int vc_reduce_node(const vc_graph *g, int32_t *deg, int32_t *S, int32_t *m, int3
     R.problem = problem;
     R.bound = bound;
     R.rules = rules;
+    R.branch = branch;
     R.deg = d_deg;
     R.io = d_io;
     const Launchers &L = width == 16 ? launchers_w16() : launchers_w32();

@@ -68,7 +68,8 @@ struct alignas(128) Control {
     alignas(128) int32_t status;       // VC_OK, or the first error code raised by any worker
     int32_t num_problems;
     int32_t max_depth;
-    int32_t pad0;
+    int32_t dbg_site;     // debug builds (VC_DEBUG_CHECKS): first failed bounds check ...
+    int32_t dbg_value;    // ... and the offending value
     unsigned long long nodes;
     unsigned long long stack_pushes;
     unsigned long long stack_pops;
@@ -109,6 +110,7 @@ struct ReduceParams {
     int32_t problem;  // kMVC / kPVC
     int32_t bound;    // best (MVC) or k (PVC)
     int32_t rules;
+    int32_t branch;   // -1: reduce as given; v >= 0: put v into S first; -2-v: put N(v) into S first
     int32_t *deg;     // n entries, in/out (device)
     int32_t *io;      // [0] = S, [1] = m, [2] = pruned (out)
 };
@@ -124,14 +126,15 @@ VC_HD inline int32_t pad16(int64_t b) { return (int32_t)((b + 15) & ~int64_t(15)
 VC_HD inline int32_t entry_bytes_for(int32_t n_max, int32_t width_bytes) {
     return 16 + pad16((int64_t)n_max * width_bytes);
 }
-// Scratch words after the entry: marks bitmask, removal list, counters and reduction slots, then
-// an optional copy of the current graph's CSR (offsets followed by neighbours).
+// Scratch after the entry: marks bitmask, dirty bitmasks, removal list, counters and reduction
+// slots, then an optional copy of the current graph's CSR (offsets followed by neighbours).
 constexpr int kScratchWords = 96;
 // Per-SM node counters are indexed by %smid modulo this power of two.
 constexpr int kSmSlots = 1024;
 VC_HD inline int32_t smem_bytes_for(int32_t n_max, int32_t width_bytes, int32_t csr_words = 0) {
     int64_t b = entry_bytes_for(n_max, width_bytes);
     b += pad16(((int64_t)n_max + 31) / 32 * 4);  // marks
+    b += pad16(((int64_t)n_max + 31) / 32 * 8);  // dirty bits (two per vertex)
     b += pad16((int64_t)n_max * 4);             // removal list
     b += kScratchWords * 4;
     b += pad16((int64_t)csr_words * 4);         // staged CSR

@@ -33,12 +33,13 @@ __global__ void __launch_bounds__(WT) greedy_kernel(Params P) {
     extern __shared__ __align__(16) uint8_t smem[];
     Worker<W, WT> w(smem, P.n_max, P.csr_words);
     w.init_scratch(P.n_max);
-    Tally t;
     if (w.tid == 0) w.sc[kScB0] = ld_relaxed(&P.ctrl->status);
     __syncthreads();
     if (w.sc[kScB0] != VC_OK) return;
+    w.dbg = P.ctrl;
     for (int p = blockIdx.x; p < P.num_problems; p += gridDim.x) {
         Ctx c = make_ctx(P, p);
+        w.cur_n = c.n;
         if (c.n == 0) {
             if (w.tid == 0) {
                 c.prob->greedy = c.prob->cover_size = c.prob->best = 0;
@@ -53,16 +54,16 @@ __global__ void __launch_bounds__(WT) greedy_kernel(Params P) {
         w.load_root(c);
         const int32_t m0 = w.hdr->m;
         for (;;) {
-            w.reduce(c, 0, kRuleDeg1 | kRuleDeg2Tri, false, t);
+            w.reduce(c, 0, kRuleDeg1 | kRuleDeg2Tri, false);
             if (w.hdr->m == 0) break;
             const int v = w.argmax(c);
             if (v < 0) break;  // unreachable: m > 0 implies a live vertex of degree >= 1
-            w.take_vertex(c, v, t);
+            w.take_vertex(c, v);
         }
         w.write_cover(c);
-        __threadfence();
         __syncthreads();
         if (w.tid == 0) {
+            __threadfence();
             Problem *pr = c.prob;
             const int32_t S = w.hdr->S;
             pr->m = m0;
@@ -180,17 +181,17 @@ __device__ void record_solution(const Params &P, Worker<W, WT> &w, const Ctx &c)
         w.sc[kScB3] = write;
     }
     __syncthreads();
-    if (w.sc[kScB3]) {
-        w.write_cover(c);
-        __threadfence();
-    }
+    if (w.sc[kScB3]) w.write_cover(c);
     __syncthreads();
     if (w.tid == 0) {
         if (write) {
-            st_release(&c.prob->cover_size, S);
             __threadfence();
+            st_release(&c.prob->cover_size, S);
         }
-        if (locked) atomicExch(&c.prob->lock, 0);
+        if (locked) {
+            __threadfence();
+            atomicExch(&c.prob->lock, 0);
+        }
     }
 }
 
@@ -199,7 +200,7 @@ __device__ void record_solution(const Params &P, Worker<W, WT> &w, const Ctx &c)
 // 1 (a root is loaded) or 2 (a worklist entry is loaded).  Sec. IV-C: the search is over when
 // the worklist is empty and no worker holds work, i.e. when no work unit is left.
 template <typename W, int WT>
-__device__ int acquire(const Params &P, Worker<W, WT> &w, Tally &t) {
+__device__ int acquire(const Params &P, Worker<W, WT> &w) {
     Control *ctrl = P.ctrl;
     if (w.tid == 0) {
         int result = 0, arg = 0;
@@ -254,16 +255,17 @@ __device__ int acquire(const Params &P, Worker<W, WT> &w, Tally &t) {
     const int result = w.sc[kScB4];
     const int arg = w.sc[kScB5];
     if (result == 1) {
+        VC_CHECK(ctrl, arg >= 0 && arg < P.num_problems, 12, arg, return 0);
         w.load_root(make_ctx(P, arg));
     } else if (result == 2) {
         const uint32_t pos = (uint32_t)arg;
         const uint32_t slot = pos & ((uint32_t)P.wl_capacity - 1u);
-        w.load_entry(P.wl_slots + (size_t)slot * P.entry_bytes, P.entry_bytes);
+        w.load_entry(P.wl_slots + (size_t)slot * P.entry_bytes, P.entry_bytes, P.n_max);
         if (w.tid == 0) {
             st_release_u32(&P.wl_seq[slot], pos + (uint32_t)P.wl_capacity);
             atomicAdd(&ctrl->wl_space, 1);
-            t.dequeues++;
-            t.bytes += P.entry_bytes;
+            w.tally[kTDequeues] += 1;
+            w.tally[kTBytes] += (unsigned long long)P.entry_bytes;
         }
     }
     return result;
@@ -277,8 +279,8 @@ __global__ void __launch_bounds__(WT) traverse_kernel(Params P) {
     extern __shared__ __align__(16) uint8_t smem[];
     Worker<W, WT> w(smem, P.n_max, P.csr_words);
     w.init_scratch(P.n_max);
-    Tally t;
     Control *ctrl = P.ctrl;
+    w.dbg = ctrl;
     const int32_t eb = P.entry_bytes;
     uint8_t *stack = P.stacks + (size_t)blockIdx.x * (size_t)P.stack_depth * (size_t)eb;
     const uint32_t wl_mask = (uint32_t)P.wl_capacity - 1u;
@@ -293,32 +295,39 @@ __global__ void __launch_bounds__(WT) traverse_kernel(Params P) {
     if (w.sc[kScB0] != VC_OK) return;
 
     while (!stop) {
+        // Every warp must have finished reading the previous node (its prune / stop / solution
+        // decision reads the header) before any warp overwrites it with the next one.
+        __syncthreads();
         // ---- acquire: local stack first (Sec. IV-A), then a root or the worklist ----
         if (top > 0) {
             --top;
-            w.load_entry(stack + (size_t)top * eb, eb);
+            w.load_entry(stack + (size_t)top * eb, eb, P.n_max);
             if (w.tid == 0) {
-                t.pops++;
-                t.bytes += eb;
+                w.tally[kTPops] += 1;
+                w.tally[kTBytes] += (unsigned long long)eb;
             }
         } else {
             if (cur >= 0 && w.tid == 0) release_unit(P, cur);
             cur = -1;
-            const int got = acquire(P, w, t);
+            const int got = acquire(P, w);
             if (got == 0) break;
             cur = w.hdr->problem;
+            VC_CHECK(ctrl, cur >= 0 && cur < P.num_problems, 1, cur, { stop = true; break; });
             c = make_ctx(P, cur);
+            VC_CHECK(ctrl, c.n >= 0 && c.n <= P.n_max, 14, c.n, { stop = true; break; });
+            w.cur_n = c.n;
             w.stage(c);
         }
+        VC_CHECK(ctrl, w.hdr->branch < c.n, 13, w.hdr->branch, { stop = true; break; });
         if (w.hdr->branch >= 0) {  // a lazily stored N(v) child: apply the removal now
-            w.take_neighbourhood(c, w.hdr->branch, t);
+            w.take_neighbourhood(c, w.hdr->branch);
             if (w.tid == 0) w.hdr->branch = -1;
         }
 
         // ---- expand nodes, continuing into the "v" child after each branch ----
         for (;;) {
             if (w.tid == 0) {
-                if ((++t.nodes & 31) == 0) atomicAdd(&ctrl->heartbeat, 1u);
+                if ((++w.tally[kTNodes] & 31) == 0) atomicAdd(&ctrl->heartbeat, 1u);
                 w.sc[kScB0] = (c.kind == kMVC) ? ld_relaxed(&c.prob->best) : c.k;
                 w.sc[kScB1] = (c.kind == kPVC) ? ld_relaxed(&c.prob->found) : 0;
                 w.sc[kScB2] = ld_relaxed(&ctrl->status);
@@ -334,7 +343,7 @@ __global__ void __launch_bounds__(WT) traverse_kernel(Params P) {
                 break;
             }
             if (w.size_exceeded(c, bound)) break;
-            if (w.reduce(c, bound, kRuleAll, true, t)) break;
+            if (w.reduce(c, bound, kRuleAll, true)) break;
             if (w.must_stop(c, bound)) break;
             if (w.hdr->m == 0) {
                 record_solution(P, w, c);
@@ -360,15 +369,15 @@ __global__ void __launch_bounds__(WT) traverse_kernel(Params P) {
                 if (w.sc[kScB3]) {  // donate (Sec. IV-A: the worklist is below its threshold)
                     const uint32_t pos = (uint32_t)w.sc[kScB4];
                     w.store_entry(P.wl_slots + (size_t)(pos & wl_mask) * eb, eb, v);
-                    __threadfence();
-                    __syncthreads();
+                    __syncthreads();  // every thread's part of the entry is written ...
                     if (w.tid == 0) {
+                        __threadfence();  // ... and ordered before the publication below
                         atomicAdd(&c.prob->units, 1);
                         atomicAdd(&ctrl->units_total, 1);
                         st_release_u32(&P.wl_seq[pos & wl_mask], pos + 1u);
                         atomicAdd(&ctrl->wl_count, 1);
-                        t.donations++;
-                        t.bytes += eb;
+                        w.tally[kTDonations] += 1;
+                        w.tally[kTBytes] += (unsigned long long)eb;
                     }
                 } else {  // push on the local stack
                     if (top >= P.stack_depth) {
@@ -379,29 +388,31 @@ __global__ void __launch_bounds__(WT) traverse_kernel(Params P) {
                     w.store_entry(stack + (size_t)top * eb, eb, v);
                     ++top;
                     if (w.tid == 0) {
-                        t.pushes++;
-                        t.bytes += eb;
-                        t.max_depth = top > t.max_depth ? top : t.max_depth;
+                        w.tally[kTPushes] += 1;
+                        w.tally[kTBytes] += (unsigned long long)eb;
+                        if ((unsigned long long)top > w.tally[kTMaxDepth]) w.tally[kTMaxDepth] = top;
                     }
                     __syncthreads();
                 }
             }
-            w.take_vertex(c, v, t);
+            w.take_vertex(c, v);
         }
     }
 
     // ---- statistics ----
-    if (w.lane == 0 && t.csr) atomicAdd(&ctrl->csr_words, t.csr);
+    __syncthreads();
     if (w.tid == 0) {
-        atomicAdd(&ctrl->nodes, t.nodes);
-        atomicAdd(&ctrl->stack_pushes, t.pushes);
-        atomicAdd(&ctrl->stack_pops, t.pops);
-        atomicAdd(&ctrl->donations, t.donations);
-        atomicAdd(&ctrl->worklist_pops, t.dequeues);
-        atomicAdd(&ctrl->rule_passes, t.passes);
-        atomicAdd(&ctrl->entry_bytes, t.bytes);
-        atomicMax(&ctrl->max_depth, t.max_depth);
-        if (P.sm_nodes) atomicAdd(&P.sm_nodes[smid() & (kSmSlots - 1)], t.nodes);
+        const unsigned long long *T = w.tally;
+        atomicAdd(&ctrl->nodes, T[kTNodes]);
+        atomicAdd(&ctrl->stack_pushes, T[kTPushes]);
+        atomicAdd(&ctrl->stack_pops, T[kTPops]);
+        atomicAdd(&ctrl->donations, T[kTDonations]);
+        atomicAdd(&ctrl->worklist_pops, T[kTDequeues]);
+        atomicAdd(&ctrl->rule_passes, T[kTPasses]);
+        atomicAdd(&ctrl->csr_words, T[kTCsr]);
+        atomicAdd(&ctrl->entry_bytes, T[kTBytes]);
+        atomicMax(&ctrl->max_depth, (int32_t)T[kTMaxDepth]);
+        if (P.sm_nodes) atomicAdd(&P.sm_nodes[smid() & (kSmSlots - 1)], T[kTNodes]);
     }
 }
 
@@ -414,7 +425,6 @@ __global__ void __launch_bounds__(WT) reduce_node_kernel(ReduceParams R) {
     extern __shared__ __align__(16) uint8_t smem[];
     Worker<W, WT> w(smem, R.n);
     w.init_scratch(R.n);
-    Tally t;
     Ctx c;
     c.off = R.offsets;
     c.adj = R.neighbors;
@@ -425,6 +435,7 @@ __global__ void __launch_bounds__(WT) reduce_node_kernel(ReduceParams R) {
     c.k = R.bound;
     c.index = 0;
     for (int v = w.tid; v < R.n; v += WT) w.d[v] = (W)R.deg[v];
+    if (R.branch == -1) w.dirty_all(R.n);  // a state from outside: every vertex is looked at
     if (w.tid == 0) {
         w.hdr->problem = 0;
         w.hdr->S = R.io[0];
@@ -432,7 +443,10 @@ __global__ void __launch_bounds__(WT) reduce_node_kernel(ReduceParams R) {
         w.hdr->branch = -1;
     }
     __syncthreads();
-    w.reduce(c, R.bound, R.rules, false, t);
+    // A branch from a fixpoint state starts clean, like a stored node in the traversal.
+    if (R.branch >= 0) w.take_vertex(c, R.branch);
+    else if (R.branch <= -2) w.take_neighbourhood(c, -2 - R.branch);
+    w.reduce(c, R.bound, R.rules, false);
     const bool pruned = w.must_stop(c, R.bound);
     for (int v = w.tid; v < R.n; v += WT) R.deg[v] = w.deg(v);
     if (w.tid == 0) {

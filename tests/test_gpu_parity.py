@@ -286,3 +286,61 @@ def test_full_batch_matches_stored_oracle_answers(vc):
         assert (g.n, g.m) == want[i][:2]
         assert sizes[i] == want[i][2], i
         check_cover(g, covers[b.vtx[i]: b.vtx[i + 1]], want[i][2])
+
+
+def _remove(g, deg, S, m, vertices):
+    """Puts a set of live vertices into S (Sec. IV-B removal), written out plainly for the test."""
+    deg = np.array(deg, dtype=np.int64)
+    chosen = set(int(v) for v in vertices)
+    for v in chosen:
+        for x in g.neighbors[g.offsets[v]:g.offsets[v + 1]].tolist():
+            if deg[x] == -1:
+                continue
+            if x in chosen:
+                if x > v:
+                    m -= 1
+            else:
+                deg[x] -= 1
+                m -= 1
+    for v in chosen:
+        deg[v] = -1
+    return deg, S + len(chosen), m
+
+
+@pytest.mark.parametrize("wt", [32, 128])
+def test_reduce_after_branch_matches_full_reduction(vc, wt):
+    # The traversal re-examines only vertices whose degree changed after a branch.  From a fixpoint
+    # state, put v (or N(v)) into S and reduce: the result must equal the oracle's full reduction
+    # of the same child state.
+    cfg = vc.make_config(worker_threads=wt)
+    for i, g in enumerate(small_graphs(30, 110000, 20, 150)):
+        for problem, slack in ((oracle.MVC, 40), (oracle.PVC, 30)):
+            bound = min(g.n, int(0.6 * g.n) + slack % 7)
+            P, S, m, pruned = oracle.reduce_node(g, g.degrees(), 0, g.m, problem, bound, 7)
+            if pruned or m == 0:
+                continue
+            live = [v for v in range(g.n) if P[v] > 0]
+            for v in live[:: max(1, len(live) // 4)]:
+                nb = [x for x in g.neighbors[g.offsets[v]:g.offsets[v + 1]].tolist() if P[x] != -1]
+                for branch, chosen in ((v, [v]), (-2 - v, nb)):
+                    child, S1, m1 = _remove(g, P, S, m, chosen)
+                    want = oracle.reduce_node(g, child, S1, m1, problem, bound, 7)
+                    got = vc.reduce_node(g.offsets, g.neighbors, P, S, m, problem, bound, 7, config=cfg,
+                                         branch=branch)
+                    assert got[0].tolist() == want[0].tolist(), (i, v, branch)
+                    assert got[1:] == want[1:], (i, v, branch, got[1:], want[1:])
+
+
+@pytest.mark.parametrize("wt", [64, 128])
+def test_batch_multiwarp_workers(vc, wt):
+    # Workers of several warps on many graphs: every warp must finish reading a node before any
+    # warp loads the next one (a race here desynchronises the block's barriers).
+    import torch
+    b = G.batch_gnp(1024)
+    want = load_batch_golden()
+    off = torch.from_numpy(b.offsets).cuda()
+    nbr = torch.from_numpy(b.neighbors).cuda()
+    for _ in range(2):
+        sizes, covers, st = vc.mvc_batch(b.vtx, b.edge, off, nbr, config=vc.make_config(worker_threads=wt))
+        assert st["worker_threads"] == wt
+        assert [int(x) for x in sizes] == [want[i][2] for i in range(1024)]
