@@ -46,6 +46,10 @@ def parse():
     ap.add_argument("--graphs", type=int, default=NUM_GRAPHS)
     ap.add_argument("--no-plain", action="store_true", help="skip the per-request plain-launch leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline leg")
+    ap.add_argument("--no-serve", action="store_true", help="skip the served-stream leg")
+    ap.add_argument("--serve-rate", type=float, default=2000.0)
+    ap.add_argument("--serve-seconds", type=float, default=5.0)
+    ap.add_argument("--serve-only", action="store_true", help="run only the served-stream leg")
     return ap.parse_args()
 
 
@@ -295,6 +299,8 @@ def run_ours(a):
             line["vs_plain_launches"] = plain_launches(vc, b, dev, stream, value)
         clocks = clk.summary()
         line["clocks"] = clocks
+        if not a.no_serve and world == 1:
+            line["serving"] = serving_leg(vc, a.serve_rate, a.serve_seconds)
         if not a.no_cpu and world == 1:
             seeds = list(range(min(CPU_SAMPLE_GRAPHS, G)))
             secs = oracle_solves(seeds, 1)
@@ -306,6 +312,97 @@ def run_ours(a):
         dist.barrier()
         dist.destroy_process_group()
     return out
+
+
+def load_serve_pool():
+    """Oracle-solved request graphs of the served workload (tests/golden/serve_pool.txt)."""
+    from paper_2204_10402_gb300 import graphs as G
+    path = os.path.join(ROOT, "tests", "golden", "serve_pool.txt")
+    pool, total = [], 0
+    for line in open(path):
+        if line.startswith("#"):
+            continue
+        seed, fam, n, d, m, mvc, nodes = line.split()
+        total += 1
+        if int(mvc) < 0:
+            continue
+        pool.append(dict(req=G.Request(0.0, 0, int(fam), int(n), float(d), 0, int(seed)), mvc=int(mvc)))
+    return pool, total
+
+
+def serving_leg(vc, rate_hz: float, duration_s: float, budget_gib: int = 64):
+    """Open-loop Poisson stream (seeded): each request picks a pool graph, is PVC with probability
+    0.7 (k = MVC-1 or MVC) else MVC.  Latency = completion seen by the host - scheduled arrival."""
+    from paper_2204_10402_gb300 import graphs as G
+    pool, total = load_serve_pool()
+    stream = G.request_stream(rate_hz, duration_s, seed=0)
+    reqs = []
+    for i, r in enumerate(stream):
+        u = G.uniform01(1 << 40, 1, i)[0]
+        e = pool[min(int(u * len(pool)), len(pool) - 1)]
+        k = e["mvc"] + r.k_offset if r.kind == 1 else 0
+        want = e["mvc"] if r.kind == 0 else int(k >= e["mvc"])
+        reqs.append((r.arrival_s, r.kind, k, e, want))
+    graphs = {}
+    for _, _, _, e, _ in reqs:
+        key = e["req"].seed
+        if key not in graphs:
+            graphs[key] = G.request_graph(e["req"])
+    max_n = max(g.n for g in graphs.values())
+    srv = vc.Server(max_n=max_n, budget_bytes=budget_gib << 30)
+    for key in list(graphs)[:32]:   # warm-up (module load, first launch)
+        srv.submit(graphs[key].offsets, graphs[key].neighbors, 0)
+    srv.drain(timeout_ms=600000)
+    ids = []
+    t0 = time.monotonic_ns() + 2_000_000
+    for arr, kind, k, e, want in reqs:
+        due = t0 + int(arr * 1e9)
+        while time.monotonic_ns() < due:
+            pass
+        g = graphs[e["req"].seed]
+        ids.append(srv.submit(g.offsets, g.neighbors, kind, k))
+    srv.drain(timeout_ms=600000)
+    infos = [srv.poll(i) for i in ids]
+    st = srv.stats()
+    srv.close()
+    lat = np.array([(x["done_ns"] - (t0 + int(r[0] * 1e9))) / 1e6 for x, r in zip(infos, reqs)])
+    wrong = sum(1 for x, r in zip(infos, reqs) if x["answer"] != r[4] or x["status"] != 0)
+    span = (max(x["done_ns"] for x in infos) - t0) / 1e9
+    # Per-request plain launches on the same GPU: each request's service time measured with one
+    # synchronous vc_mvc / vc_pvc call (device-resident CSR), then the same arrivals replayed
+    # through a FIFO queue of one server.
+    import torch
+    dev_graphs = {key: (torch.from_numpy(g.offsets).cuda(), torch.from_numpy(g.neighbors if g.neighbors.size else np.zeros(1, np.int32)).cuda()) for key, g in graphs.items()}
+    sample = reqs[: min(len(reqs), 2000)]
+    service = []
+    for arr, kind, k, e, want in sample:
+        off, nbr = dev_graphs[e["req"].seed]
+        t = time.perf_counter()
+        if kind == 0:
+            vc.mvc(off, nbr, want_cover=False)
+        else:
+            vc.pvc(off, nbr, k, want_cover=False)
+        service.append(time.perf_counter() - t)
+    finish, plain_lat = 0.0, []
+    for (arr, *_), sv in zip(sample, service):
+        start = max(arr, finish)
+        finish = start + sv
+        plain_lat.append((finish - arr) * 1e3)
+    plain_lat = np.array(plain_lat)
+    return {
+        "workload": f"Poisson {rate_hz:g} req/s for {duration_s:g} s, 70% PVC (k = MVC-1 or MVC) / 30% MVC, "
+                    f"graphs from a pool of {len(pool)} oracle-solved requests "
+                    f"({total - len(pool)} of {total} candidates rejected over a 50K-node oracle cap)",
+        "requests": len(reqs), "wrong_answers": wrong,
+        "solves_per_s": len(reqs) / span,
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                       "p999": float(np.percentile(lat, 99.9))},
+        "plain_launches": {"sample": len(sample), "solves_per_s_capacity": len(sample) / sum(service),
+                           "latency_ms": {"p50": float(np.percentile(plain_lat, 50)),
+                                          "p99": float(np.percentile(plain_lat, 99)),
+                                          "p999": float(np.percentile(plain_lat, 99.9))}},
+        "server": {k: st[k] for k in ("launches", "epochs", "nodes_visited", "workers", "worker_threads")},
+    }
 
 
 def plain_launches(vc, b, dev, stream, batched_value):
@@ -333,6 +430,13 @@ def plain_launches(vc, b, dev, stream, batched_value):
 
 def main():
     a = parse()
+    if a.serve_only:
+        import paper_2204_10402_gb300 as vc
+        from paper_2204_10402_gb300 import build
+        build.build()
+        vc.load()
+        print(json.dumps(serving_leg(vc, a.serve_rate, a.serve_seconds)), flush=True)
+        return
     if a.impl == "reference":
         run_reference(a)
     else:

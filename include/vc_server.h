@@ -1,0 +1,82 @@
+/*
+ * vc_server.h - serving exact vertex cover with continuous batching (libvc).
+ *
+ * A server keeps one persistent traversal launch (the hybrid stack + worklist search of Sec. IV-A,
+ * rules of Sec. II-B / IV-D, termination of Sec. IV-C) running while requests arrive.  Requests
+ * admitted while others are being searched join the running launch: idle workers claim them, run
+ * their greedy bound (Sec. II-B) and search them through the shared worklist, whose entries carry
+ * the request's slot, so the work of many requests overlaps on the device.  The paper solves one
+ * graph per launch; the serving layer is this library's own.
+ *
+ * Admission: every request reserves a slot and a range of the device graph arena (its CSR and
+ * cover mask).  Stacks and worklist are sized once, at creation, for graphs of up to max_n
+ * vertices (depth max_n + 3 entries of the degree-array size per worker), so any accepted request
+ * fits them.  A request whose bytes do not fit the arena right now waits in a host queue and is
+ * admitted when earlier requests finish; it is never refused for lack of room unless it alone is
+ * larger than the whole arena.
+ *
+ * Graphs are copied at submission (host pointers only; same CSR rules as vc.h, checked on the host);
+ * the caller's buffers can be reused as soon as vc_server_submit returns.  All functions are safe
+ * to call from several host threads.  Errors as in vc.h.
+ */
+#ifndef VC_SERVER_H
+#define VC_SERVER_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#include "vc.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vc_server vc_server;
+
+/* State of one request.  Times are steady-clock nanoseconds (same clock for all requests). */
+typedef struct {
+    int32_t done;       /* 1 once the answer is known */
+    int32_t answer;     /* MVC: minimum cover size; PVC: 1 if a cover of size <= k exists, else 0 */
+    int32_t status;     /* VC_OK or the error that ended the request */
+    int32_t greedy;     /* greedy upper bound computed for the request (-1 if none) */
+    int64_t submit_ns;  /* vc_server_submit was called */
+    int64_t admit_ns;   /* the request was uploaded and published to the device */
+    int64_t done_ns;    /* the host saw the device's completion record */
+} vc_request_info;
+
+typedef struct {
+    int64_t completed, pending, in_flight;  /* requests */
+    int64_t launches;                       /* persistent launches started so far */
+    int64_t epochs;                         /* arena / slot epochs completed */
+    int64_t nodes_visited;                  /* tree nodes over all finished launches */
+    int32_t workers, worker_threads, slots_per_epoch;
+    int64_t arena_bytes;
+} vc_server_counters;
+
+/* Creates a server on the current device.  device_bytes_budget (0 = 8 GiB) bounds the device
+ * memory it holds: half goes to the per-worker stacks (which sets the worker count), a quarter to
+ * the graph arena.  max_n is the largest graph it accepts.  cfg (may be NULL) picks the worker size,
+ * width, worklist capacity and donation threshold as in vc.h. */
+int vc_server_create(const vc_config *cfg, size_t device_bytes_budget, int32_t max_n, vc_server **server);
+
+/* Queues a request: kind 0 = MVC, 1 = PVC with parameter k.  Returns at once with its id. */
+int vc_server_submit(vc_server *server, const vc_graph *g, int32_t kind, int32_t k, uint64_t *request_id);
+
+/* Reads a request's state (see vc_request_info). */
+int vc_server_poll(vc_server *server, uint64_t request_id, vc_request_info *info);
+
+/* Waits until every submitted request has finished (timeout_ms <= 0: no limit; VC_ETIMEOUT if the
+ * limit passes first). */
+int vc_server_drain(vc_server *server, int64_t timeout_ms);
+
+/* Server-wide counters. */
+int vc_server_stats(vc_server *server, vc_server_counters *out);
+
+/* Finishes the requests still queued or in flight, stops the launch and frees everything. */
+int vc_server_destroy(vc_server *server);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VC_SERVER_H */

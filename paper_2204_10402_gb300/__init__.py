@@ -27,7 +27,9 @@ MVC, PVC = 0, 1
 RULE_DEG1, RULE_DEG2TRI, RULE_HIGH, RULE_ALL = 1, 2, 4, 7
 
 EXPORTED = ["vc_mvc", "vc_pvc", "vc_mvc_batch", "vc_greedy", "vc_reduce_node", "vc_last_sm_nodes",
-            "vc_release", "vc_strerror", "vc_version", "vc_mvc_noalloc"]
+            "vc_release", "vc_strerror", "vc_version", "vc_mvc_noalloc",
+            "vc_server_create", "vc_server_submit", "vc_server_poll", "vc_server_drain", "vc_server_stats",
+            "vc_server_destroy"]
 NOALLOC_MAX_N = 512
 
 
@@ -64,6 +66,25 @@ class Stats(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("done", ctypes.c_int32), ("answer", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("greedy", ctypes.c_int32), ("submit_ns", ctypes.c_int64), ("admit_ns", ctypes.c_int64),
+                ("done_ns", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class ServerCounters(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_int64), ("pending", ctypes.c_int64), ("in_flight", ctypes.c_int64),
+                ("launches", ctypes.c_int64), ("epochs", ctypes.c_int64), ("nodes_visited", ctypes.c_int64),
+                ("workers", ctypes.c_int32), ("worker_threads", ctypes.c_int32),
+                ("slots_per_epoch", ctypes.c_int32), ("arena_bytes", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 _lib = None
 
 
@@ -91,12 +112,19 @@ def load(path: str | None = None):
     lib.vc_reduce_node.argtypes = [gp, P, i32p, i32p, i32, i32, i32, i32, cp, P, i32p]
     lib.vc_last_sm_nodes.argtypes = [P, i32]
     lib.vc_mvc_noalloc.argtypes = [gp, cp, P, P, i32p, sp]
+    lib.vc_server_create.argtypes = [cp, ctypes.c_size_t, i32, ctypes.POINTER(ctypes.c_void_p)]
+    lib.vc_server_submit.argtypes = [P, gp, i32, i32, ctypes.POINTER(ctypes.c_uint64)]
+    lib.vc_server_poll.argtypes = [P, ctypes.c_uint64, ctypes.POINTER(RequestInfo)]
+    lib.vc_server_drain.argtypes = [P, i64]
+    lib.vc_server_stats.argtypes = [P, ctypes.POINTER(ServerCounters)]
+    lib.vc_server_destroy.argtypes = [P]
     lib.vc_release.argtypes = []
     lib.vc_strerror.argtypes = [ctypes.c_int]
     lib.vc_strerror.restype = ctypes.c_char_p
     lib.vc_version.argtypes = []
     for name in ("vc_mvc", "vc_pvc", "vc_mvc_batch", "vc_greedy", "vc_reduce_node", "vc_last_sm_nodes",
-                 "vc_release", "vc_version", "vc_mvc_noalloc"):
+                 "vc_release", "vc_version", "vc_mvc_noalloc", "vc_server_create", "vc_server_submit",
+                 "vc_server_poll", "vc_server_drain", "vc_server_stats", "vc_server_destroy"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -321,3 +349,61 @@ def last_sm_nodes() -> np.ndarray:
 
 def release():
     _check(load().vc_release(), "vc_release")
+
+
+class Server:
+    """Serving with continuous batching (include/vc_server.h): one persistent launch searches all
+    admitted requests at once; requests submitted while it runs join it.
+
+        with Server(max_n=3000) as srv:
+            rid = srv.submit(offsets, neighbors, MVC)
+            srv.drain()
+            srv.poll(rid)["answer"]
+    """
+
+    def __init__(self, max_n: int, budget_bytes: int = 0, config: Config | None = None):
+        lib = load()
+        h = ctypes.c_void_p()
+        _check(lib.vc_server_create(ctypes.byref(config) if config else None, int(budget_bytes), int(max_n),
+                                    ctypes.byref(h)), "vc_server_create")
+        self._h = h
+        self._lib = lib
+
+    def submit(self, offsets, neighbors, kind: int, k: int = 0) -> int:
+        g, keep = _graph(offsets, neighbors)
+        if g.on_device:
+            raise ValueError("Server.submit takes host arrays")
+        rid = ctypes.c_uint64(0)
+        _check(self._lib.vc_server_submit(self._h, ctypes.byref(g), int(kind), int(k), ctypes.byref(rid)),
+               "vc_server_submit")
+        return int(rid.value)
+
+    def poll(self, rid: int) -> dict:
+        info = RequestInfo()
+        _check(self._lib.vc_server_poll(self._h, ctypes.c_uint64(rid), ctypes.byref(info)), "vc_server_poll")
+        return info.as_dict()
+
+    def drain(self, timeout_ms: int = 0):
+        _check(self._lib.vc_server_drain(self._h, int(timeout_ms)), "vc_server_drain")
+
+    def stats(self) -> dict:
+        c = ServerCounters()
+        _check(self._lib.vc_server_stats(self._h, ctypes.byref(c)), "vc_server_stats")
+        return c.as_dict()
+
+    def close(self):
+        if self._h:
+            _check(self._lib.vc_server_destroy(self._h), "vc_server_destroy")
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -53,10 +53,14 @@ __global__ void validate_kernel(const int32_t *offsets, const int32_t *neighbors
     }
 }
 
-__global__ void init_worklist_kernel(uint32_t *seq, int32_t capacity, Control *ctrl) {
+__global__ void init_worklist_kernel(uint32_t *seq, int32_t capacity, Control *ctrl,
+                                     unsigned long long *claim_state) {
     const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < capacity) seq[i] = (uint32_t)i;
-    if (i == 0) ctrl->wl_space = capacity;
+    if (i == 0) {
+        ctrl->wl_space = capacity;
+        if (claim_state) *claim_state &= 0xffffffffull;  // a new serving launch is open again
+    }
 }
 
 int launch_validate(const int32_t *offsets, const int32_t *neighbors, const Problem *probs,
@@ -71,8 +75,9 @@ int launch_validate(const int32_t *offsets, const int32_t *neighbors, const Prob
     return cudaPeekAtLastError() == cudaSuccess ? VC_OK : VC_ECUDA;
 }
 
-int launch_init_worklist(uint32_t *seq, int32_t capacity, Control *ctrl, cudaStream_t s) {
-    init_worklist_kernel<<<(capacity + 255) / 256, 256, 0, s>>>(seq, capacity, ctrl);
+int launch_init_worklist(uint32_t *seq, int32_t capacity, Control *ctrl, cudaStream_t s,
+                         unsigned long long *claim_state) {
+    init_worklist_kernel<<<(capacity + 255) / 256, 256, 0, s>>>(seq, capacity, ctrl, claim_state);
     return cudaPeekAtLastError() == cudaSuccess ? VC_OK : VC_ECUDA;
 }
 

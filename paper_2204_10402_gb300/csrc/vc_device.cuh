@@ -67,6 +67,11 @@ __device__ __forceinline__ void st_release_u32(uint32_t *p, uint32_t v) {
 __device__ __forceinline__ void st_release(int32_t *p, int32_t v) {
     asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
 __device__ __forceinline__ uint64_t globaltimer_ns() {
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -123,16 +128,18 @@ struct Ctx {
     int32_t index;
 };
 
+// The problem record's constants are read through L2 (.cg): a serving launch receives records
+// written by the host while it runs, which no L1 may hold stale.
 __device__ __forceinline__ Ctx make_ctx(const Params &P, int32_t p) {
     Ctx c;
     Problem *pr = P.problems + p;
-    c.off = P.offsets + pr->off_base;
-    c.adj = P.neighbors + pr->adj_base;
+    c.off = P.offsets + __ldcg(&pr->off_base);
+    c.adj = P.neighbors + __ldcg(&pr->adj_base);
     c.prob = pr;
-    c.cover = P.cover + pr->cover_base;
-    c.n = pr->n;
-    c.kind = pr->kind;
-    c.k = pr->k;
+    c.cover = P.cover + __ldcg(&pr->cover_base);
+    c.n = __ldcg(&pr->n);
+    c.kind = __ldcg(&pr->kind);
+    c.k = __ldcg(&pr->k);
     c.index = p;
     return c;
 }

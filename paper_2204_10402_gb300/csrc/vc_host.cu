@@ -236,11 +236,12 @@ int run(Workspace &ws, const Spec &spec, const vc_config *cfg_in, cudaStream_t s
     VC_RC(grow(ws.ctrl, sizeof(Control)));
     VC_RC(grow(ws.cover, sizeof(int32_t) * (size_t)std::max<int64_t>(spec.total_vertices, 1)));
     VC_RC(grow(ws.sm_nodes, sizeof(unsigned long long) * (size_t)kSmSlots));
-    const size_t staging = sizeof(Problem) * (size_t)G + sizeof(int64_t) * (size_t)G + sizeof(Control);
-    VC_RC(grow_pinned(ws, staging));
+    const size_t adj_len_at = sizeof(Problem) * (size_t)G;
+    const size_t ctrl_at = (adj_len_at + sizeof(int64_t) * (size_t)G + 127) & ~size_t(127);
+    VC_RC(grow_pinned(ws, ctrl_at + sizeof(Control)));
     Problem *h_probs = reinterpret_cast<Problem *>(ws.pinned);
-    int64_t *h_adj_len = reinterpret_cast<int64_t *>(h_probs + G);
-    Control *h_ctrl = reinterpret_cast<Control *>(h_adj_len + G);
+    int64_t *h_adj_len = reinterpret_cast<int64_t *>(static_cast<uint8_t *>(ws.pinned) + adj_len_at);
+    Control *h_ctrl = reinterpret_cast<Control *>(static_cast<uint8_t *>(ws.pinned) + ctrl_at);
     std::memcpy(h_probs, spec.probs.data(), sizeof(Problem) * (size_t)G);
     std::memcpy(h_adj_len, spec.adj_len.data(), sizeof(int64_t) * (size_t)G);
 

@@ -35,7 +35,9 @@ struct alignas(16) EntryHeader {
     int32_t branch;   // pending N(branch) removal, or -1
 };
 
-struct alignas(16) Problem {
+// One record per problem, each on its own 128-byte line: records of different problems never
+// share a line (no false sharing between their atomics, no stale neighbours in a serving launch).
+struct alignas(128) Problem {
     // constants, written by the host
     int64_t off_base;    // first offset of this graph in the packed offsets array
     int64_t adj_base;    // first neighbour of this graph in the packed neighbour array
@@ -52,7 +54,7 @@ struct alignas(16) Problem {
     int32_t greedy;      // greedy upper bound
     int32_t units;       // work units alive: unclaimed root + worklist entries + workers holding work
     int32_t done;        // 1 once the last unit was released
-    int32_t pad;
+    int32_t tag;         // serving: completion tag the host waits for (0 otherwise)
 };
 
 // Launch-wide control block.  Words that many workers hit with atomics or polls each own a
@@ -100,6 +102,15 @@ struct Params {
     int64_t idle_timeout_ns;
     const volatile int32_t *cancel;
     unsigned long long *sm_nodes;  // per-SM node counters
+    // Serving (a persistent launch that takes requests while it runs); all zero otherwise.
+    int32_t serving;
+    uint32_t sub_mask;               // submission ring capacity - 1 (a power of two)
+    const uint32_t *sub_ring;        // slot indices of admitted requests, written by the host's copies
+    const uint32_t *sub_tail;        // number of published submissions
+    unsigned long long *claim_state; // bit 32: the launch is closing; low 32 bits: requests claimed
+    const int32_t *close_now;        // nonzero: idle workers close the launch at once
+    int32_t *completion;             // host-mapped, 4 ints per slot: {tag, answer, status, greedy}
+    int64_t linger_ns;               // idle time after which an empty launch closes
 };
 
 // Debug single-node reduction arguments.

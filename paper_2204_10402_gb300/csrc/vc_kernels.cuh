@@ -23,11 +23,56 @@ __global__ void validate_kernel(const int32_t *offsets, const int32_t *neighbors
                                 const int64_t *adj_len, int32_t num_problems, int64_t total_vertices,
                                 Control *ctrl);
 
-__global__ void init_worklist_kernel(uint32_t *seq, int32_t capacity, Control *ctrl);
+__global__ void init_worklist_kernel(uint32_t *seq, int32_t capacity, Control *ctrl,
+                                     unsigned long long *claim_state);
 
 // ------------------------------------------------------------------------------------------------
-// Greedy upper bound (Sec. II-B; the oracle's reading R5): one worker per problem.
+// Greedy upper bound (Sec. II-B; the oracle's reading R5): repeat {degree-one and
+// degree-two-triangle rules to a fixpoint; stop when edgeless; put the maximum-degree vertex into
+// S}.  Leaves the greedy cover in the problem's cover mask and best / greedy / cover_size (and the
+// PVC found flag when the greedy cover already fits) in its record.  Returns whether a search is
+// still needed (uniform across the block).
 // ------------------------------------------------------------------------------------------------
+template <typename W, int WT>
+__device__ bool greedy_solve(const Params &P, Worker<W, WT> &w, Ctx &c) {
+    w.cur_n = c.n;
+    if (c.n == 0) {
+        __syncthreads();
+        if (w.tid == 0) {
+            c.prob->greedy = c.prob->cover_size = c.prob->best = 0;
+            c.prob->m = 0;
+            if (c.kind == kPVC && c.k >= 0) c.prob->found = 1;
+        }
+        __syncthreads();
+        return false;
+    }
+    w.stage(c);
+    w.load_root(c);
+    const int32_t m0 = w.hdr->m;
+    for (;;) {
+        w.reduce(c, 0, kRuleDeg1 | kRuleDeg2Tri, false);
+        if (w.hdr->m == 0) break;
+        const int v = w.argmax(c);
+        if (v < 0) break;  // unreachable: m > 0 implies a live vertex of degree >= 1
+        w.take_vertex(c, v);
+    }
+    w.write_cover(c);
+    const int32_t S = w.hdr->S;
+    __syncthreads();
+    if (w.tid == 0) {
+        __threadfence();
+        Problem *pr = c.prob;
+        pr->m = m0;
+        pr->greedy = S;
+        pr->best = S;
+        pr->cover_size = S;
+        if (c.kind == kPVC && c.k >= 0 && S <= c.k) pr->found = 1;  // greedy already fits (reading R6)
+    }
+    __syncthreads();
+    // An edgeless graph needs no search; PVC needs none when k < 0 or the greedy cover fits.
+    return c.kind == kMVC ? S > 0 : (c.k >= 0 && S > c.k);
+}
+
 template <typename W, int WT>
 __global__ void __launch_bounds__(WT) greedy_kernel(Params P) {
     extern __shared__ __align__(16) uint8_t smem[];
@@ -39,49 +84,12 @@ __global__ void __launch_bounds__(WT) greedy_kernel(Params P) {
     w.dbg = P.ctrl;
     for (int p = blockIdx.x; p < P.num_problems; p += gridDim.x) {
         Ctx c = make_ctx(P, p);
-        w.cur_n = c.n;
-        if (c.n == 0) {
-            if (w.tid == 0) {
-                c.prob->greedy = c.prob->cover_size = c.prob->best = 0;
-                c.prob->m = 0;
-                if (c.kind == kPVC && c.k >= 0) c.prob->found = 1;
-                c.prob->units = 0;
-                c.prob->done = 1;
-            }
-            continue;
-        }
-        w.stage(c);
-        w.load_root(c);
-        const int32_t m0 = w.hdr->m;
-        for (;;) {
-            w.reduce(c, 0, kRuleDeg1 | kRuleDeg2Tri, false);
-            if (w.hdr->m == 0) break;
-            const int v = w.argmax(c);
-            if (v < 0) break;  // unreachable: m > 0 implies a live vertex of degree >= 1
-            w.take_vertex(c, v);
-        }
-        w.write_cover(c);
-        __syncthreads();
+        const bool search = greedy_solve(P, w, c);
         if (w.tid == 0) {
-            __threadfence();
-            Problem *pr = c.prob;
-            const int32_t S = w.hdr->S;
-            pr->m = m0;
-            pr->greedy = S;
-            pr->best = S;
-            pr->cover_size = S;
-            bool search;
-            if (c.kind == kMVC) {
-                search = S > 0;  // an edgeless graph needs no search
-            } else {
-                if (c.k >= 0 && S <= c.k) pr->found = 1;  // greedy already fits (reading R6)
-                search = c.k >= 0 && S > c.k;
-            }
-            pr->units = search ? 1 : 0;
-            pr->done = search ? 0 : 1;
+            c.prob->units = search ? 1 : 0;
+            c.prob->done = search ? 0 : 1;
             if (search) atomicAdd(&P.ctrl->units_total, 1);
         }
-        __syncthreads();
     }
 }
 
@@ -141,10 +149,22 @@ __device__ __forceinline__ long long wl_take(const Params &P) {
 }
 
 // Gives back the work unit a worker held for problem p (its node and local stack are finished).
+// The worker that releases a problem's last unit completes it; a serving launch then writes the
+// answer into the host-visible completion record, tag last.
 __device__ __forceinline__ void release_unit(const Params &P, int32_t p) {
     Problem *pr = P.problems + p;
     __threadfence();
-    if (atomicSub(&pr->units, 1) == 1) st_release(&pr->done, 1);
+    if (atomicSub(&pr->units, 1) == 1) {
+        st_release(&pr->done, 1);
+        if (P.completion) {
+            volatile int32_t *rec = P.completion + 4 * (size_t)p;
+            rec[1] = __ldcg(&pr->kind) == kMVC ? ld_relaxed(&pr->best) : ld_relaxed(&pr->found);
+            rec[2] = ld_relaxed(&P.ctrl->status);
+            rec[3] = ld_relaxed(&pr->greedy);
+            __threadfence_system();
+            rec[0] = __ldcg(&pr->tag);
+        }
+    }
     atomicSub(&P.ctrl->units_total, 1);
 }
 
@@ -195,6 +215,65 @@ __device__ void record_solution(const Params &P, Worker<W, WT> &w, const Ctx &c)
     }
 }
 
+// Serving idle loop (thread 0): a worklist entry (returns 2, ticket in arg), a newly admitted
+// request (returns 3, slot in arg; the caller holds its unit and runs its greedy bound), or 0 when
+// the launch closes.  Claiming and closing go through one 64-bit word (closing bit | claimed
+// count), so a claim and a close can never both succeed; a claimer counts its unit before it
+// claims, so a closer that saw no unit left cannot overtake a claim in progress.  An empty launch
+// closes after linger_ns idle (or at once when the host asks), and the host relaunches when new
+// requests arrive.
+__device__ __forceinline__ int serve_wait(const Params &P, int &arg) {
+    Control *ctrl = P.ctrl;
+    uint64_t t0 = globaltimer_ns();
+    uint32_t beat = ld_relaxed_u32(&ctrl->heartbeat);
+    unsigned sleep_ns = 64 + (blockIdx.x & 63);
+    for (;;) {
+        if (ld_relaxed(&ctrl->status) != VC_OK) return 0;
+        const long long pos = wl_take(P);
+        if (pos >= 0) {
+            arg = (int)(uint32_t)pos;
+            return 2;
+        }
+        if (pos == -2) return 0;
+        const unsigned long long st = ld_relaxed_u64(P.claim_state);
+        if (st >> 32) return 0;  // the launch is closing
+        const uint32_t claimed = (uint32_t)st;
+        if (claimed < ld_relaxed_u32(P.sub_tail)) {
+            atomicAdd(&ctrl->units_total, 1);
+            if (atomicCAS(P.claim_state, st, st + 1ull) == st) {
+                const uint32_t slot = ld_relaxed_u32(&P.sub_ring[claimed & P.sub_mask]);
+                atomicExch(&P.problems[slot].units, 1);
+                arg = (int)slot;
+                return 3;
+            }
+            atomicSub(&ctrl->units_total, 1);
+            continue;
+        }
+        const uint64_t now = globaltimer_ns();
+        if (ld_acquire(&ctrl->units_total) == 0) {
+            if (ld_relaxed(P.close_now) != 0 || now - t0 > (uint64_t)P.linger_ns) {
+                if (atomicCAS(P.claim_state, st, st | (1ull << 32)) == st) return 0;
+                continue;
+            }
+        } else {
+            const uint32_t b = ld_relaxed_u32(&ctrl->heartbeat);
+            if (b != beat) {
+                beat = b;
+                t0 = now;
+            } else if (now - t0 > (uint64_t)P.idle_timeout_ns) {
+                raise_status(ctrl, VC_ETIMEOUT);
+                return 0;
+            }
+        }
+        if (P.cancel && *P.cancel) {
+            raise_status(ctrl, VC_ECANCELLED);
+            return 0;
+        }
+        __nanosleep(sleep_ns);
+        if (sleep_ns < 8192) sleep_ns += sleep_ns >> 1;
+    }
+}
+
 // Finds the next node for a worker whose local stack is empty: an unclaimed root first, then the
 // worklist; idles with a growing sleep while other workers still hold work.  Returns 0 (stop),
 // 1 (a root is loaded) or 2 (a worklist entry is loaded).  Sec. IV-C: the search is over when
@@ -213,7 +292,9 @@ __device__ int acquire(const Params &P, Worker<W, WT> &w) {
                 break;
             }
         }
-        if (!result) {
+        if (!result && P.serving) {
+            result = serve_wait(P, arg);
+        } else if (!result) {
             // The wait ends with work, with the end of the search, or after idle_timeout_ns during
             // which no busy worker showed progress (heartbeat unchanged): a stalled launch reports
             // VC_ETIMEOUT instead of spinning forever.  Sleeps grow geometrically (with a per-worker
@@ -257,6 +338,8 @@ __device__ int acquire(const Params &P, Worker<W, WT> &w) {
     if (result == 1) {
         VC_CHECK(ctrl, arg >= 0 && arg < P.num_problems, 12, arg, return 0);
         w.load_root(make_ctx(P, arg));
+    } else if (result == 3) {
+        VC_CHECK(ctrl, arg >= 0 && arg < P.num_problems, 18, arg, return 0);
     } else if (result == 2) {
         const uint32_t pos = (uint32_t)arg;
         const uint32_t slot = pos & ((uint32_t)P.wl_capacity - 1u);
@@ -309,14 +392,22 @@ __global__ void __launch_bounds__(WT) traverse_kernel(Params P) {
         } else {
             if (cur >= 0 && w.tid == 0) release_unit(P, cur);
             cur = -1;
-            const int got = acquire(P, w);
+            int got = acquire(P, w);
             if (got == 0) break;
-            cur = w.hdr->problem;
-            VC_CHECK(ctrl, cur >= 0 && cur < P.num_problems, 1, cur, { stop = true; break; });
-            c = make_ctx(P, cur);
-            VC_CHECK(ctrl, c.n >= 0 && c.n <= P.n_max, 14, c.n, { stop = true; break; });
-            w.cur_n = c.n;
-            w.stage(c);
+            if (got == 3) {  // serving: a new request; this worker holds its unit
+                cur = w.sc[kScB5];
+                c = make_ctx(P, cur);
+                VC_CHECK(ctrl, c.n >= 0 && c.n <= P.n_max, 19, c.n, { stop = true; break; });
+                if (!greedy_solve(P, w, c)) continue;  // answered by the greedy bound: release
+                w.load_root(c);
+            } else {
+                cur = w.hdr->problem;
+                VC_CHECK(ctrl, cur >= 0 && cur < P.num_problems, 1, cur, { stop = true; break; });
+                c = make_ctx(P, cur);
+                VC_CHECK(ctrl, c.n >= 0 && c.n <= P.n_max, 14, c.n, { stop = true; break; });
+                w.cur_n = c.n;
+                w.stage(c);
+            }
         }
         VC_CHECK(ctrl, w.hdr->branch < c.n, 13, w.hdr->branch, { stop = true; break; });
         if (w.hdr->branch >= 0) {  // a lazily stored N(v) child: apply the removal now

@@ -23,6 +23,7 @@ const Launchers &launchers_w32();
 int launch_validate(const int32_t *offsets, const int32_t *neighbors, const Problem *probs,
                     const int64_t *adj_len, int32_t num_problems, int64_t total_vertices, Control *ctrl,
                     cudaStream_t s);
-int launch_init_worklist(uint32_t *seq, int32_t capacity, Control *ctrl, cudaStream_t s);
+int launch_init_worklist(uint32_t *seq, int32_t capacity, Control *ctrl, cudaStream_t s,
+                         unsigned long long *claim_state = nullptr);
 
 }  // namespace vc

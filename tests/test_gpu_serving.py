@@ -1,0 +1,112 @@
+"""Serving with continuous batching: every answer is the same alone and in the mix (integers,
+compared exactly), requests submitted while a launch runs join it, and admission under a tiny
+memory budget queues requests instead of failing them."""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2204_10402_gb300 import graphs as G
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def vc():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_2204_10402_gb300 as vc
+    from paper_2204_10402_gb300 import build
+    build.build()
+    vc.load()
+    return vc
+
+
+def mixed_requests(count, seed0):
+    """(graph, kind, k, expected answer) with answers from the CPU oracle."""
+    out = []
+    for i in range(count):
+        u = G.uniform01(seed0 + i, 4)
+        if u[0] < 0.5:
+            n = 20 + int(u[1] * 70)
+            g = G.gnp(n, 0.05 + 0.15 * u[2], seed0 + i, draw_offset=4)
+        else:
+            n = 100 + int(u[1] * 900)
+            g = G.chung_lu(n, 4.0 + 2.5 * u[2], seed0 + i)
+        best, _, _ = oracle.mvc(g)
+        if u[3] < 0.3:
+            out.append((g, 0, 0, best))
+        else:
+            k = best - (1 if u[3] < 0.65 else 0)
+            out.append((g, 1, k, int(k >= best)))
+    return out
+
+
+def run_alone(vc, reqs):
+    got = []
+    for g, kind, k, _ in reqs:
+        if kind == 0:
+            got.append(vc.mvc(g.offsets, g.neighbors, want_cover=False).value)
+        else:
+            got.append(vc.pvc(g.offsets, g.neighbors, k, want_cover=False).value)
+    return got
+
+
+def test_mix_equals_alone_and_oracle(vc):
+    reqs = mixed_requests(80, 120000)
+    alone = run_alone(vc, reqs)
+    assert alone == [r[3] for r in reqs]
+    with vc.Server(max_n=1000) as srv:
+        ids = [srv.submit(g.offsets, g.neighbors, kind, k) for g, kind, k, _ in reqs]
+        srv.drain(timeout_ms=120000)
+        infos = [srv.poll(i) for i in ids]
+        st = srv.stats()
+    assert all(x["done"] and x["status"] == 0 for x in infos)
+    assert [x["answer"] for x in infos] == alone
+    assert st["completed"] == len(reqs) and st["launches"] >= 1
+
+
+def test_trickled_requests_join_a_running_launch(vc):
+    reqs = mixed_requests(40, 130000)
+    with vc.Server(max_n=1000) as srv:
+        ids = []
+        for g, kind, k, _ in reqs:
+            ids.append(srv.submit(g.offsets, g.neighbors, kind, k))
+            time.sleep(0.0005)
+        srv.drain(timeout_ms=120000)
+        infos = [srv.poll(i) for i in ids]
+    assert [x["answer"] for x in infos] == [r[3] for r in reqs]
+    assert all(x["submit_ns"] <= x["admit_ns"] <= x["done_ns"] for x in infos)
+
+
+def test_small_budget_queues_instead_of_failing(vc):
+    # A 1 MiB budget leaves a 256 KiB graph arena (about 85 of these graphs): most requests wait
+    # in the host queue, and the arena is used up and restarted at least once.
+    graphs = [G.gnp(90, 0.07, 140000 + i) for i in range(150)]
+    want = [oracle.mvc(g)[0] for g in graphs]
+    with vc.Server(max_n=120, budget_bytes=1 << 20) as srv:
+        ids = [srv.submit(g.offsets, g.neighbors, 0) for g in graphs]
+        srv.drain(timeout_ms=120000)
+        got = [srv.poll(i) for i in ids]
+        st = srv.stats()
+    assert [x["answer"] for x in got] == want
+    assert all(x["status"] == 0 for x in got)
+    assert st["epochs"] >= 1
+
+
+def test_rejects_bad_requests(vc):
+    with vc.Server(max_n=50) as srv:
+        big = G.gnp(60, 0.1, 1)
+        with pytest.raises(vc.VCError):
+            srv.submit(big.offsets, big.neighbors, 0)
+        g = G.cycle(6)
+        bad = g.neighbors.copy()
+        bad[0] = 4
+        with pytest.raises(vc.VCError):
+            srv.submit(g.offsets, bad, 0)
+        rid = srv.submit(g.offsets, g.neighbors, 1, -1)   # k < 0 is answered at once
+        assert srv.poll(rid)["done"] == 1 and srv.poll(rid)["answer"] == 0
+        rid = srv.submit(g.offsets, g.neighbors, 0)
+        srv.drain(timeout_ms=60000)
+        assert srv.poll(rid)["answer"] == 3
