@@ -29,7 +29,8 @@ RULE_DEG1, RULE_DEG2TRI, RULE_HIGH, RULE_ALL = 1, 2, 4, 7
 EXPORTED = ["vc_mvc", "vc_pvc", "vc_mvc_batch", "vc_greedy", "vc_reduce_node", "vc_last_sm_nodes",
             "vc_release", "vc_strerror", "vc_version", "vc_mvc_noalloc",
             "vc_server_create", "vc_server_submit", "vc_server_poll", "vc_server_drain", "vc_server_stats",
-            "vc_server_destroy"]
+            "vc_server_destroy", "vc_plan_create_mvc_batch", "vc_plan_launch", "vc_plan_results",
+            "vc_plan_destroy"]
 NOALLOC_MAX_N = 512
 
 
@@ -118,13 +119,18 @@ def load(path: str | None = None):
     lib.vc_server_drain.argtypes = [P, i64]
     lib.vc_server_stats.argtypes = [P, ctypes.POINTER(ServerCounters)]
     lib.vc_server_destroy.argtypes = [P]
+    lib.vc_plan_create_mvc_batch.argtypes = [i32, P, P, P, P, i32, cp, ctypes.POINTER(ctypes.c_void_p)]
+    lib.vc_plan_launch.argtypes = [P, P]
+    lib.vc_plan_results.argtypes = [P, P, P, P, i32, sp]
+    lib.vc_plan_destroy.argtypes = [P]
     lib.vc_release.argtypes = []
     lib.vc_strerror.argtypes = [ctypes.c_int]
     lib.vc_strerror.restype = ctypes.c_char_p
     lib.vc_version.argtypes = []
     for name in ("vc_mvc", "vc_pvc", "vc_mvc_batch", "vc_greedy", "vc_reduce_node", "vc_last_sm_nodes",
                  "vc_release", "vc_version", "vc_mvc_noalloc", "vc_server_create", "vc_server_submit",
-                 "vc_server_poll", "vc_server_drain", "vc_server_stats", "vc_server_destroy"):
+                 "vc_server_poll", "vc_server_drain", "vc_server_stats", "vc_server_destroy",
+                 "vc_plan_create_mvc_batch", "vc_plan_launch", "vc_plan_results", "vc_plan_destroy"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -401,6 +407,61 @@ class Server:
 
     def __exit__(self, *exc):
         self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class BatchPlan:
+    """Batched MVC captured as one CUDA graph (include/vc_plan.h): build once, launch many times.
+
+        plan = BatchPlan(vtx, edge, offsets, neighbors)
+        plan.launch(stream); sizes, covers, stats = plan.results(stream)
+    """
+
+    def __init__(self, vtx, edge, offsets, neighbors, config: Config | None = None):
+        lib = load()
+        self._lib = lib
+        vtx = _host_i32(vtx)
+        edge = _host_i32(edge)
+        self.G = vtx.size - 1
+        self.total_n = int(vtx[-1])
+        on_dev = _is_cuda_tensor(offsets)
+        if on_dev:
+            off_p = offsets.contiguous().data_ptr()
+            nb_p = neighbors.contiguous().data_ptr() if neighbors.numel() else 0
+        else:
+            o = _host_i32(offsets)
+            nbr = _host_i32(neighbors)
+            if nbr.size == 0:
+                nbr = np.zeros(1, dtype=np.int32)
+            self._keep = (o, nbr)
+            off_p, nb_p = o.ctypes.data, nbr.ctypes.data
+        h = ctypes.c_void_p()
+        _check(lib.vc_plan_create_mvc_batch(self.G, vtx.ctypes.data, edge.ctypes.data, off_p, nb_p,
+                                            1 if on_dev else 0, ctypes.byref(config) if config else None,
+                                            ctypes.byref(h)), "vc_plan_create_mvc_batch")
+        self._h = h
+
+    def launch(self, stream=None):
+        _check(self._lib.vc_plan_launch(self._h, _stream(stream)), "vc_plan_launch")
+
+    def results(self, stream=None, want_covers: bool = False):
+        sizes = np.zeros(max(self.G, 1), dtype=np.int32)
+        covers = np.zeros(max(self.total_n, 1), dtype=np.int32) if want_covers else None
+        st = Stats()
+        _check(self._lib.vc_plan_results(self._h, _stream(stream), sizes.ctypes.data,
+                                         covers.ctypes.data if covers is not None else None, 0,
+                                         ctypes.byref(st)), "vc_plan_results")
+        return sizes[: self.G], covers, st.as_dict()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _check(self._lib.vc_plan_destroy(self._h), "vc_plan_destroy")
+            self._h = None
 
     def __del__(self):
         try:

@@ -344,3 +344,26 @@ def test_batch_multiwarp_workers(vc, wt):
         sizes, covers, st = vc.mvc_batch(b.vtx, b.edge, off, nbr, config=vc.make_config(worker_threads=wt))
         assert st["worker_threads"] == wt
         assert [int(x) for x in sizes] == [want[i][2] for i in range(1024)]
+
+
+def test_batch_plan_graph_replay(vc):
+    # The batch captured as one CUDA graph, replayed three times: identical answers every time,
+    # equal to the oracle's, with valid covers.
+    import torch
+    b = G.batch_gnp(512)
+    want = load_batch_golden()
+    plan = vc.BatchPlan(b.vtx, b.edge, torch.from_numpy(b.offsets).cuda(), torch.from_numpy(b.neighbors).cuda())
+    for _ in range(3):
+        plan.launch()
+        sizes, covers, st = plan.results(want_covers=True)
+        assert [int(x) for x in sizes] == [want[i][2] for i in range(512)]
+        for i, g in enumerate(b.graphs[:64]):
+            check_cover(g, covers[b.vtx[i]: b.vtx[i + 1]], want[i][2])
+        assert st["nodes_visited"] > 0 and st["kernel_ms"] > 0
+    plan.close()
+    bad = G.cycle(5)
+    nb = bad.neighbors.copy()
+    nb[0] = 3
+    pb = G.pack([bad])
+    with pytest.raises(vc.VCError):
+        vc.BatchPlan(pb.vtx, pb.edge, pb.offsets, nb)
