@@ -72,8 +72,9 @@ typedef struct {
     float donate_threshold;     /* donate while the worklist holds fewer than this fraction of its capacity */
     int64_t idle_timeout_ns;    /* VC_ETIMEOUT once an idle worker saw no progress anywhere for this long (default 20 s) */
     int32_t skip_validation;    /* 1: trust the CSR and skip the device check */
-    int32_t stage_csr;          /* 1: copy each worker's current graph CSR into shared memory when it fits
-                                   (fewer resident workers, shared-memory latency); 0: read it through L1 */
+    int32_t stage_csr;          /* shared-memory copy of each worker's current graph: 0 = its offsets when
+                                   n <= 1024, 1 = offsets and neighbour lists when they fit (fewer resident
+                                   workers), -1 = nothing (all CSR reads through L1) */
     const volatile int32_t *cancel;  /* optional host-mapped or device flag; nonzero aborts with VC_ECANCELLED */
 } vc_config;
 
@@ -96,6 +97,9 @@ typedef struct {
     int32_t status;             /* device status word (VC_OK or an error code) */
     float kernel_ms;            /* traversal kernel time (CUDA events on the call's stream) */
     float total_ms;             /* whole call (validation, greedy, traversal, copies) */
+    int64_t trace_ns[4];        /* builds with -DVC_TRACE: worker time waiting for work, in reduction rules and
+                                   stop checks, branching, recording solutions (Sec. V-D breakdown); else 0 */
+    int64_t idle_polls;         /* builds with -DVC_TRACE: idle-loop iterations; else 0 */
 } vc_stats;
 
 /* Minimum Vertex Cover (Sec. II-A, II-B, IV).

@@ -61,10 +61,13 @@ class Stats(ctypes.Structure):
                 ("max_depth", ctypes.c_int32), ("greedy_ub", ctypes.c_int32), ("workers", ctypes.c_int32),
                 ("worker_threads", ctypes.c_int32), ("width", ctypes.c_int32), ("csr_staged", ctypes.c_int32),
                 ("status", ctypes.c_int32),
-                ("kernel_ms", ctypes.c_float), ("total_ms", ctypes.c_float)]
+                ("kernel_ms", ctypes.c_float), ("total_ms", ctypes.c_float),
+                ("trace_ns", ctypes.c_int64 * 4), ("idle_polls", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
-        return {name: getattr(self, name) for name, _ in self._fields_}
+        d = {name: getattr(self, name) for name, _ in self._fields_}
+        d["trace_ns"] = list(self.trace_ns)
+        return d
 
 
 class RequestInfo(ctypes.Structure):

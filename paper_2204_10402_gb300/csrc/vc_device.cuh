@@ -25,6 +25,7 @@ namespace vc {
 
 constexpr unsigned kFull = 0xffffffffu;
 
+
 // Scratch word indices.
 enum : int {
     kScCount = 0,   // entries in the removal list
@@ -35,7 +36,7 @@ enum : int {
     kScB3 = 5,
     kScB4 = 6,
     kScB5 = 7,
-    kScKeys = 32,   // 32 x u64 per-warp argmax keys (words 32..95)
+    kScKeys = 48,   // 32 x u64 per-warp argmax keys (words 48..111)
 };
 
 // ------------------------------------------------------------------------------------------------
@@ -155,9 +156,29 @@ enum TallySlot : int {
     kTCsr,
     kTBytes,
     kTMaxDepth,
+    kTWaitNs,     // VC_TRACE: time spent waiting for work (worklist, roots, idle)
+    kTReduceNs,   // VC_TRACE: reduction rules and stop check
+    kTBranchNs,   // VC_TRACE: argmax, donate / push, child construction
+    kTSolutionNs, // VC_TRACE: solution capture
+    kTIdlePolls,  // VC_TRACE: idle-loop iterations
     kTallySlots
 };
-constexpr int kScTally = 8;  // first scratch word of the tally (8-byte aligned)
+constexpr int kScTally = 8;  // first scratch word of the tally (8-byte aligned, 16 slots)
+static_assert(kScTally + 2 * kTallySlots <= 40, "tally overlaps the argmax keys");
+
+// VC_TRACE builds time the activities of Sec. V-D (thread 0 of each worker, %globaltimer).
+#ifdef VC_TRACE
+#define VC_TRACE_NOW() globaltimer_ns()
+#define VC_TRACE_ADD(w, slot, t0)                                         \
+    do {                                                                  \
+        if ((w).tid == 0) (w).tally[slot] += globaltimer_ns() - (t0);    \
+    } while (0)
+#else
+#define VC_TRACE_NOW() 0ull
+#define VC_TRACE_ADD(w, slot, t0) \
+    do {                          \
+    } while (0)
+#endif
 
 // ------------------------------------------------------------------------------------------------
 // Worker
@@ -178,6 +199,7 @@ struct Worker {
     int32_t entry_bytes;
     int32_t csr_words;
     int32_t staged;  // problem whose CSR is in csr, or -1
+    bool staged_full;  // the neighbour lists are staged too
     Control *dbg;    // where debug builds report failed checks (may be null)
     int32_t cur_n;   // vertices of the current graph (for the debug checks)
     int32_t n_cap;   // shared-memory capacity in vertices
@@ -196,6 +218,7 @@ struct Worker {
         csr = sc + kScratchWords;
         csr_words = csr_capacity;
         staged = -1;
+        staged_full = false;
         dbg = nullptr;
         cur_n = n_max;
         n_cap = n_max;
@@ -203,6 +226,16 @@ struct Worker {
         lane = tid & 31;
         warp = tid >> 5;
         entry_bytes = eb;
+    }
+
+    // Worker-wide barriers: a one-warp worker needs only a warp barrier (and a warp vote).
+    __device__ __forceinline__ void sync() const {
+        if constexpr (WT == 32) __syncwarp();
+        else __syncthreads();
+    }
+    __device__ __forceinline__ bool sync_or(bool p) const {
+        if constexpr (WT == 32) return __any_sync(kFull, p);
+        else return __syncthreads_or(p);
     }
 
     __device__ __forceinline__ int deg(int v) const { return (int)d[v]; }
@@ -255,25 +288,28 @@ struct Worker {
             dirty[i] = 0ull;
         }
         for (int i = tid; i < kScratchWords; i += WT) sc[i] = 0;
-        __syncthreads();
+        sync();
     }
 
-    // Points c at a shared-memory copy of its graph's CSR (copied when the problem changes), if the
-    // launch reserved room for it and the graph fits.
+    // Points c at a shared-memory copy of its graph's offsets -- and of its neighbour lists too
+    // when the launch reserved room for them -- copied when the problem changes.
     __device__ void stage(Ctx &c) {
         if (csr_words == 0) return;
         const int n1 = c.n + 1;
+        if (n1 > csr_words) return;  // does not fit: keep reading global memory
         if (c.index != staged) {
             const int len = c.off[c.n];
-            if (n1 + len > csr_words) return;  // does not fit: keep reading global memory
-            __syncthreads();                    // nobody still reads the previous copy
+            const bool full = n1 + len <= csr_words;
+            sync();  // nobody still reads the previous copy
             for (int i = tid; i < n1; i += WT) csr[i] = c.off[i];
-            for (int i = tid; i < len; i += WT) csr[n1 + i] = c.adj[i];
+            if (full)
+                for (int i = tid; i < len; i += WT) csr[n1 + i] = c.adj[i];
             staged = c.index;
-            __syncthreads();
+            staged_full = full;
+            sync();
         }
         c.off = csr;
-        c.adj = csr + n1;
+        if (staged_full) c.adj = csr + n1;
     }
 
     // ---- node loading / storing ---------------------------------------------------------------
@@ -281,7 +317,7 @@ struct Worker {
     // Root node of a problem (Sec. IV-A: the search starts from the whole graph): degrees from the
     // CSR, |S| = 0, m = offsets[n] / 2.
     __device__ void load_root(const Ctx &c) {
-        __syncthreads();  // no warp still reads the node being replaced
+        sync();  // no warp still reads the node being replaced
         for (int v = tid; v < c.n; v += WT) d[v] = (W)(c.off[v + 1] - c.off[v]);
         dirty_all(c.n);
         if (tid == 0) {
@@ -290,18 +326,18 @@ struct Worker {
             hdr->m = c.off[c.n] / 2;
             hdr->branch = -1;
         }
-        __syncthreads();
+        sync();
     }
 
     // Copies an entry of `bytes` (header + degree array of the entry's graph) from global memory.
     // Loads go through L2 only (.cg) because the producer may be another SM.
     __device__ void load_entry(const uint8_t *src, int32_t bytes, int32_t n_max) {
-        __syncthreads();  // no warp still reads the node being replaced
+        sync();  // no warp still reads the node being replaced
         const int4 *s = reinterpret_cast<const int4 *>(src);
         int4 *t = reinterpret_cast<int4 *>(hdr);
         for (int i = tid; i < bytes / 16; i += WT) t[i] = __ldcg(s + i);
         dirty_none(n_max);
-        __syncthreads();
+        sync();
     }
 
     // Copies the current node to global memory with its header's branch field set to `branch`.
@@ -321,7 +357,9 @@ struct Worker {
     // the list lose one degree, m loses every edge with a listed endpoint (an edge between two
     // listed vertices once), |S| grows by the list length.  One warp per listed vertex, its lanes
     // splitting the vertex's adjacency list.  Must follow a barrier that ended the proposals.
-    __device__ void apply_list(const Ctx &c) {
+    // (A flattened walk over all listed vertices' lists at once issues fewer dependent loads but
+    // measured slower: the traversal is bound by instruction issue, not by load latency.)
+    __device__ __forceinline__ void apply_list(const Ctx &c) {
         int cnt = sc[kScCount];
         VC_CHECK(dbg, cnt >= 0 && cnt <= c.n, 3, cnt, cnt = 0);
         int edges = 0, words = 0;
@@ -347,7 +385,7 @@ struct Worker {
         edges = __reduce_add_sync(kFull, edges);
         if (lane == 0 && edges) atomicAdd(&sc[kScEdges], edges);
         if (lane == 0 && words) atomicAdd(&tally[kTCsr], (unsigned long long)words);
-        __syncthreads();
+        sync();
         for (int i = tid; i < cnt; i += WT) {
             const int u = list[i];
             VC_CHECK(dbg, u >= 0 && u < c.n, 16, u, continue);
@@ -360,13 +398,13 @@ struct Worker {
             sc[kScEdges] = 0;
             sc[kScCount] = 0;
         }
-        __syncthreads();
+        sync();
     }
 
     // Ends a pass: returns true (and applies the removal) iff some thread proposed a vertex.
     __device__ __forceinline__ bool finish_pass(const Ctx &c, bool proposed) {
         if (tid == 0) tally[kTPasses] += 1;
-        if (!__syncthreads_or(proposed)) return false;
+        if (!sync_or(proposed)) return false;
         apply_list(c);
         return true;
     }
@@ -490,7 +528,9 @@ struct Worker {
     }
 
     // High-degree: a vertex whose degree exceeds the threshold enters S.  Threshold best-|S|-1
-    // for MVC, k-|S| for PVC (`bound` is best or k).
+    // for MVC, k-|S| for PVC (`bound` is best or k).  (Computing argmax keys in this scan, to
+    // spare argmax() its own scan after the last pass, measured 5 % slower: every pass paid for
+    // keys only the last one needs.)
     __device__ bool pass_high_degree(const Ctx &c, int32_t bound) {
         const int thr = (c.kind == kMVC) ? bound - hdr->S - 1 : bound - hdr->S;
         bool proposed = false;
@@ -558,7 +598,7 @@ struct Worker {
         key = warp_max_u64(key);
         if constexpr (kWarps > 1) {
             if (lane == 0) keys[warp] = key;
-            __syncthreads();
+            sync();
             unsigned long long k2 = lane < kWarps ? keys[lane] : 0ull;
             key = warp_max_u64(k2);
         }
@@ -569,7 +609,7 @@ struct Worker {
     __device__ void take_vertex(const Ctx &c, int v) {
         VC_CHECK(dbg, v >= 0 && v < c.n, 5, v, return);
         if (tid == 0) propose(v);
-        __syncthreads();
+        sync();
         apply_list(c);
     }
 
@@ -586,7 +626,7 @@ struct Worker {
             }
         }
         if (tid == 0) atomicAdd(&tally[kTCsr], (unsigned long long)(hi - lo));
-        if (__syncthreads_or(proposed)) apply_list(c);
+        if (sync_or(proposed)) apply_list(c);
     }
 
     // Writes the current node's S as a 0/1 mask.

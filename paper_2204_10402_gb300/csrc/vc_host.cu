@@ -200,9 +200,13 @@ int run(Workspace &ws, const Spec &spec, const vc_config *cfg_in, cudaStream_t s
         if (spec.adj_len[i] < 0) known = false;
         else csr_need = std::max<int64_t>(csr_need, (int64_t)spec.probs[i].n + 1 + spec.adj_len[i]);
     }
+    // Default: stage only the offsets (n+1 ints) of graphs up to kOffsetStageN vertices; with
+    // stage_csr = 1 stage the neighbour lists too; with stage_csr = -1 stage nothing.
     int32_t csr_words = 0;
     if (known && cfg.stage_csr > 0 && csr_need > 0 && csr_need * 4 <= (int64_t)ws.smem_optin)
         csr_words = (int32_t)csr_need;
+    else
+        csr_words = default_csr_words(n_max, cfg.stage_csr);
     int smem = smem_bytes_for(n_max, wbytes, csr_words);
     if (smem > ws.smem_optin && csr_words) {
         csr_words = 0;
@@ -217,7 +221,7 @@ int run(Workspace &ws, const Spec &spec, const vc_config *cfg_in, cudaStream_t s
     const int32_t eb = entry_bytes_for(n_max, wbytes);
 
     // ---- worklist sizing (Sec. V-A explores 128K-512K entries, threshold 0.25-1.0 x size) ----
-    int cap = cfg.worklist_capacity > 0 ? next_pow2(cfg.worklist_capacity) : next_pow2(std::max(1024, 2 * workers));
+    int cap = cfg.worklist_capacity > 0 ? next_pow2(cfg.worklist_capacity) : default_worklist_capacity(eb);
     float frac = cfg.donate_threshold > 0.f ? cfg.donate_threshold : 0.5f;
     int threshold = (int)std::max<double>(0.0, std::min<double>(cap, (double)frac * cap));
     if (cfg.donate_threshold < 0.f) threshold = 0;  // never donate (stress setting)
@@ -353,6 +357,8 @@ void fill_stats(vc_stats *st, const Result &r, double total_ms, int32_t greedy) 
     st->rule_passes = (int64_t)r.ctrl.rule_passes;
     st->csr_words = (int64_t)r.ctrl.csr_words;
     st->entry_bytes_moved = (int64_t)r.ctrl.entry_bytes;
+    for (int i = 0; i < 4; ++i) st->trace_ns[i] = (int64_t)r.ctrl.trace_ns[i];
+    st->idle_polls = (int64_t)r.ctrl.idle_polls;
     st->max_depth = r.ctrl.max_depth;
     st->greedy_ub = greedy;
     st->workers = r.workers;

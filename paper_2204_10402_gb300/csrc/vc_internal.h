@@ -80,6 +80,8 @@ struct alignas(128) Control {
     unsigned long long rule_passes;
     unsigned long long csr_words;
     unsigned long long entry_bytes;
+    unsigned long long trace_ns[4];  // VC_TRACE builds: ns waiting for work, reducing, branching, solutions
+    unsigned long long idle_polls;   // VC_TRACE builds: idle-loop iterations
 };
 
 // Kernel arguments (passed by value).
@@ -139,7 +141,7 @@ VC_HD inline int32_t entry_bytes_for(int32_t n_max, int32_t width_bytes) {
 }
 // Scratch after the entry: marks bitmask, dirty bitmasks, removal list, counters and reduction
 // slots, then an optional copy of the current graph's CSR (offsets followed by neighbours).
-constexpr int kScratchWords = 96;
+constexpr int kScratchWords = 112;
 // Per-SM node counters are indexed by %smid modulo this power of two.
 constexpr int kSmSlots = 1024;
 VC_HD inline int32_t smem_bytes_for(int32_t n_max, int32_t width_bytes, int32_t csr_words = 0) {
@@ -150,6 +152,22 @@ VC_HD inline int32_t smem_bytes_for(int32_t n_max, int32_t width_bytes, int32_t 
     b += kScratchWords * 4;
     b += pad16((int64_t)csr_words * 4);         // staged CSR
     return (int32_t)b;
+}
+
+// Default worklist capacity: the largest power of two up to 262144 entries whose slots fit in
+// 1 GiB (Sec. V-A tries 128K-512K entries; measured on the 4096-graph batch: 16K entries 388 ms,
+// 64K 348 ms, 256K 290 ms per launch).
+VC_HD inline int32_t default_worklist_capacity(int32_t entry_bytes) {
+    int64_t cap = 262144;
+    while (cap > 1024 && cap * (int64_t)entry_bytes > (int64_t(1) << 30)) cap >>= 1;
+    return (int32_t)cap;
+}
+
+// Shared-memory CSR staging by default: the offsets (n+1 ints) of graphs with up to
+// kOffsetStageN vertices; nothing for larger graphs (their workers share the CSR through L1).
+constexpr int32_t kOffsetStageN = 1024;
+VC_HD inline int32_t default_csr_words(int32_t n_max, int32_t stage_csr) {
+    return (stage_csr == 0 && n_max <= kOffsetStageN) ? n_max + 1 : 0;
 }
 
 }  // namespace vc

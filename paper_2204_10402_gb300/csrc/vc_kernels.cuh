@@ -37,13 +37,13 @@ template <typename W, int WT>
 __device__ bool greedy_solve(const Params &P, Worker<W, WT> &w, Ctx &c) {
     w.cur_n = c.n;
     if (c.n == 0) {
-        __syncthreads();
+        w.sync();
         if (w.tid == 0) {
             c.prob->greedy = c.prob->cover_size = c.prob->best = 0;
             c.prob->m = 0;
             if (c.kind == kPVC && c.k >= 0) c.prob->found = 1;
         }
-        __syncthreads();
+        w.sync();
         return false;
     }
     w.stage(c);
@@ -58,7 +58,7 @@ __device__ bool greedy_solve(const Params &P, Worker<W, WT> &w, Ctx &c) {
     }
     w.write_cover(c);
     const int32_t S = w.hdr->S;
-    __syncthreads();
+    w.sync();
     if (w.tid == 0) {
         __threadfence();
         Problem *pr = c.prob;
@@ -68,7 +68,7 @@ __device__ bool greedy_solve(const Params &P, Worker<W, WT> &w, Ctx &c) {
         pr->cover_size = S;
         if (c.kind == kPVC && c.k >= 0 && S <= c.k) pr->found = 1;  // greedy already fits (reading R6)
     }
-    __syncthreads();
+    w.sync();
     // An edgeless graph needs no search; PVC needs none when k < 0 or the greedy cover fits.
     return c.kind == kMVC ? S > 0 : (c.k >= 0 && S > c.k);
 }
@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(WT) greedy_kernel(Params P) {
     Worker<W, WT> w(smem, P.n_max, P.csr_words);
     w.init_scratch(P.n_max);
     if (w.tid == 0) w.sc[kScB0] = ld_relaxed(&P.ctrl->status);
-    __syncthreads();
+    w.sync();
     if (w.sc[kScB0] != VC_OK) return;
     w.dbg = P.ctrl;
     for (int p = blockIdx.x; p < P.num_problems; p += gridDim.x) {
@@ -200,9 +200,9 @@ __device__ void record_solution(const Params &P, Worker<W, WT> &w, const Ctx &c)
         }
         w.sc[kScB3] = write;
     }
-    __syncthreads();
+    w.sync();
     if (w.sc[kScB3]) w.write_cover(c);
-    __syncthreads();
+    w.sync();
     if (w.tid == 0) {
         if (write) {
             __threadfence();
@@ -325,6 +325,9 @@ __device__ int acquire(const Params &P, Worker<W, WT> &w) {
                     raise_status(ctrl, VC_ETIMEOUT);
                     break;
                 }
+#ifdef VC_TRACE
+                w.tally[kTIdlePolls] += 1;
+#endif
                 __nanosleep(sleep_ns);
                 if (sleep_ns < 8192) sleep_ns += sleep_ns >> 1;
             }
@@ -332,7 +335,7 @@ __device__ int acquire(const Params &P, Worker<W, WT> &w) {
         w.sc[kScB4] = result;
         w.sc[kScB5] = arg;
     }
-    __syncthreads();
+    w.sync();
     const int result = w.sc[kScB4];
     const int arg = w.sc[kScB5];
     if (result == 1) {
@@ -357,8 +360,10 @@ __device__ int acquire(const Params &P, Worker<W, WT> &w) {
 // ------------------------------------------------------------------------------------------------
 // Persistent hybrid traversal (Sec. IV-A): one worker per thread block.
 // ------------------------------------------------------------------------------------------------
+// At most 64 registers per thread, so every worker size keeps 2048 threads resident per SM
+// (measured: the uncapped build used 72 registers, fit 28 one-warp blocks per SM and ran 4 % slower).
 template <typename W, int WT>
-__global__ void __launch_bounds__(WT) traverse_kernel(Params P) {
+__global__ void __launch_bounds__(WT, 1024 / WT) traverse_kernel(Params P) {
     extern __shared__ __align__(16) uint8_t smem[];
     Worker<W, WT> w(smem, P.n_max, P.csr_words);
     w.init_scratch(P.n_max);
@@ -374,13 +379,13 @@ __global__ void __launch_bounds__(WT) traverse_kernel(Params P) {
     c.n = 0;
 
     if (w.tid == 0) w.sc[kScB0] = ld_relaxed(&ctrl->status);
-    __syncthreads();
+    w.sync();
     if (w.sc[kScB0] != VC_OK) return;
 
     while (!stop) {
         // Every warp must have finished reading the previous node (its prune / stop / solution
         // decision reads the header) before any warp overwrites it with the next one.
-        __syncthreads();
+        w.sync();
         // ---- acquire: local stack first (Sec. IV-A), then a root or the worklist ----
         if (top > 0) {
             --top;
@@ -392,7 +397,9 @@ __global__ void __launch_bounds__(WT) traverse_kernel(Params P) {
         } else {
             if (cur >= 0 && w.tid == 0) release_unit(P, cur);
             cur = -1;
+            const unsigned long long t_wait = VC_TRACE_NOW();
             int got = acquire(P, w);
+            VC_TRACE_ADD(w, kTWaitNs, t_wait);
             if (got == 0) break;
             if (got == 3) {  // serving: a new request; this worker holds its unit
                 cur = w.sc[kScB5];
@@ -423,7 +430,7 @@ __global__ void __launch_bounds__(WT) traverse_kernel(Params P) {
                 w.sc[kScB1] = (c.kind == kPVC) ? ld_relaxed(&c.prob->found) : 0;
                 w.sc[kScB2] = ld_relaxed(&ctrl->status);
             }
-            __syncthreads();
+            w.sync();
             const int32_t bound = w.sc[kScB0];  // one snapshot of best per node (reading R3)
             if (w.sc[kScB2] != VC_OK) {
                 stop = true;
@@ -434,12 +441,17 @@ __global__ void __launch_bounds__(WT) traverse_kernel(Params P) {
                 break;
             }
             if (w.size_exceeded(c, bound)) break;
-            if (w.reduce(c, bound, kRuleAll, true)) break;
-            if (w.must_stop(c, bound)) break;
+            const unsigned long long t_red = VC_TRACE_NOW();
+            const bool pruned = w.reduce(c, bound, kRuleAll, true) || w.must_stop(c, bound);
+            VC_TRACE_ADD(w, kTReduceNs, t_red);
+            if (pruned) break;
             if (w.hdr->m == 0) {
+                const unsigned long long t_sol = VC_TRACE_NOW();
                 record_solution(P, w, c);
+                VC_TRACE_ADD(w, kTSolutionNs, t_sol);
                 break;
             }
+            const unsigned long long t_br = VC_TRACE_NOW();
             const int v = w.argmax(c);
             if (v < 0) {  // unreachable: m > 0 implies a live vertex of degree >= 1
                 if (w.tid == 0) raise_status(ctrl, VC_EINVAL);
@@ -456,11 +468,11 @@ __global__ void __launch_bounds__(WT) traverse_kernel(Params P) {
                     w.sc[kScB3] = pos >= 0;
                     w.sc[kScB4] = (int32_t)(uint32_t)(pos >= 0 ? pos : 0);
                 }
-                __syncthreads();
+                w.sync();
                 if (w.sc[kScB3]) {  // donate (Sec. IV-A: the worklist is below its threshold)
                     const uint32_t pos = (uint32_t)w.sc[kScB4];
                     w.store_entry(P.wl_slots + (size_t)(pos & wl_mask) * eb, eb, v);
-                    __syncthreads();  // every thread's part of the entry is written ...
+                    w.sync();  // every thread's part of the entry is written ...
                     if (w.tid == 0) {
                         __threadfence();  // ... and ordered before the publication below
                         atomicAdd(&c.prob->units, 1);
@@ -483,15 +495,16 @@ __global__ void __launch_bounds__(WT) traverse_kernel(Params P) {
                         w.tally[kTBytes] += (unsigned long long)eb;
                         if ((unsigned long long)top > w.tally[kTMaxDepth]) w.tally[kTMaxDepth] = top;
                     }
-                    __syncthreads();
+                    w.sync();
                 }
             }
             w.take_vertex(c, v);
+            VC_TRACE_ADD(w, kTBranchNs, t_br);
         }
     }
 
     // ---- statistics ----
-    __syncthreads();
+    w.sync();
     if (w.tid == 0) {
         const unsigned long long *T = w.tally;
         atomicAdd(&ctrl->nodes, T[kTNodes]);
@@ -502,6 +515,13 @@ __global__ void __launch_bounds__(WT) traverse_kernel(Params P) {
         atomicAdd(&ctrl->rule_passes, T[kTPasses]);
         atomicAdd(&ctrl->csr_words, T[kTCsr]);
         atomicAdd(&ctrl->entry_bytes, T[kTBytes]);
+#ifdef VC_TRACE
+        atomicAdd(&ctrl->trace_ns[0], T[kTWaitNs]);
+        atomicAdd(&ctrl->trace_ns[1], T[kTReduceNs]);
+        atomicAdd(&ctrl->trace_ns[2], T[kTBranchNs]);
+        atomicAdd(&ctrl->trace_ns[3], T[kTSolutionNs]);
+        atomicAdd(&ctrl->idle_polls, T[kTIdlePolls]);
+#endif
         atomicMax(&ctrl->max_depth, (int32_t)T[kTMaxDepth]);
         if (P.sm_nodes) atomicAdd(&P.sm_nodes[smid() & (kSmSlots - 1)], T[kTNodes]);
     }
@@ -533,7 +553,7 @@ __global__ void __launch_bounds__(WT) reduce_node_kernel(ReduceParams R) {
         w.hdr->m = R.io[1];
         w.hdr->branch = -1;
     }
-    __syncthreads();
+    w.sync();
     // A branch from a fixpoint state starts clean, like a stored node in the traversal.
     if (R.branch >= 0) w.take_vertex(c, R.branch);
     else if (R.branch <= -2) w.take_neighbourhood(c, -2 - R.branch);

@@ -98,7 +98,8 @@ extern "C" int vc_mvc_noalloc(const vc_graph *g, const vc_config *cfg_in, void *
     const int n = g->n;
     const int wt = cfg.worker_threads ? cfg.worker_threads : worker_threads_for(n);
     const int wbytes = 2;
-    const int smem = smem_bytes_for(n, wbytes, 0);
+    const int32_t csr_words = default_csr_words(n, cfg.stage_csr);
+    const int smem = smem_bytes_for(n, wbytes, csr_words);
     const Launchers &L = launchers_w16();
     int per_sm = 0;
     if (int rc = L.occupancy(wt, smem, &per_sm)) return rc;
@@ -151,6 +152,7 @@ extern "C" int vc_mvc_noalloc(const vc_graph *g, const vc_config *cfg_in, void *
     P.cover = d_cover;
     P.wl_capacity = kNoAllocWorklist;
     P.wl_threshold = kNoAllocWorklist / 2;
+    P.csr_words = csr_words;
     P.idle_timeout_ns = cfg.idle_timeout_ns > 0 ? cfg.idle_timeout_ns : 20000000000ll;
     P.cancel = cfg.cancel;
     P.sm_nodes = d_sm;

@@ -93,7 +93,8 @@ int vc_plan_create_mvc_batch(int32_t G, const int32_t *vtx, const int32_t *edge,
         return VC_EINVAL;
     }
     pl->wt = cfg.worker_threads ? cfg.worker_threads : (n_max <= 160 ? 32 : n_max <= 640 ? 64 : n_max <= 2560 ? 128 : 256);
-    pl->smem = smem_bytes_for(n_max, pl->width / 8, 0);
+    const int32_t csr_words = default_csr_words(n_max, cfg.stage_csr);
+    pl->smem = smem_bytes_for(n_max, pl->width / 8, csr_words);
     const Launchers &L = pl->width == 16 ? launchers_w16() : launchers_w32();
     int per_sm = 0;
     if (pl->smem > (int)prop.sharedMemPerBlockOptin || L.occupancy(pl->wt, pl->smem, &per_sm) != VC_OK || per_sm <= 0) {
@@ -103,7 +104,10 @@ int vc_plan_create_mvc_batch(int32_t G, const int32_t *vtx, const int32_t *edge,
     pl->workers = cfg.num_workers > 0 ? cfg.num_workers : prop.multiProcessorCount * per_sm;
     pl->eb = entry_bytes_for(n_max, pl->width / 8);
     int cap = 1;
-    while (cap < std::max(1024, cfg.worklist_capacity > 0 ? cfg.worklist_capacity : 2 * pl->workers)) cap <<= 1;
+    if (cfg.worklist_capacity > 0)
+        while (cap < cfg.worklist_capacity) cap <<= 1;
+    else
+        cap = default_worklist_capacity(pl->eb);
     pl->cap = cap;
     const float frac = cfg.donate_threshold > 0.f ? cfg.donate_threshold : 0.5f;
     const int threshold = cfg.donate_threshold < 0.f ? 0 : std::max(0, std::min(cap, (int)(frac * cap)));
@@ -177,6 +181,7 @@ int vc_plan_create_mvc_batch(int32_t G, const int32_t *vtx, const int32_t *edge,
     P.wl_seq = reinterpret_cast<uint32_t *>(b + o_seq);
     P.wl_capacity = cap;
     P.wl_threshold = threshold;
+    P.csr_words = csr_words;
     P.idle_timeout_ns = cfg.idle_timeout_ns > 0 ? cfg.idle_timeout_ns : 20000000000ll;
     P.cancel = cfg.cancel;
     P.sm_nodes = reinterpret_cast<unsigned long long *>(b + o_smn);
@@ -241,6 +246,8 @@ int vc_plan_results(vc_plan *pl, void *stream, int32_t *sizes_out, int32_t *cove
         stats->rule_passes = (int64_t)c.rule_passes;
         stats->csr_words = (int64_t)c.csr_words;
         stats->entry_bytes_moved = (int64_t)c.entry_bytes;
+        for (int i = 0; i < 4; ++i) stats->trace_ns[i] = (int64_t)c.trace_ns[i];
+        stats->idle_polls = (int64_t)c.idle_polls;
         stats->max_depth = c.max_depth;
         stats->workers = pl->workers;
         stats->worker_threads = pl->wt;

@@ -69,6 +69,7 @@ struct vc_server {
     size_t budget = 0;
     // variant
     int wt = 0, width = 16, smem = 0, workers = 0, eb = 0, depth = 0, cap = 0, threshold = 0;
+    int32_t csr_words = 0;
     int32_t slots = 0;          // problem slots per epoch (power of two, also the ring capacity)
     size_t arena_bytes = 0;
     // device memory
@@ -137,6 +138,7 @@ Params serve_params(vc_server *s) {
     P.wl_seq = s->wl_seq;
     P.wl_capacity = s->cap;
     P.wl_threshold = s->threshold;
+    P.csr_words = s->csr_words;
     P.idle_timeout_ns = s->cfg.idle_timeout_ns > 0 ? s->cfg.idle_timeout_ns : 20000000000ll;
     P.cancel = s->cfg.cancel;
     P.sm_nodes = s->sm_nodes;
@@ -399,7 +401,8 @@ int vc_server_create(const vc_config *cfg, size_t device_bytes_budget, int32_t m
         return VC_EINVAL;
     }
     s->wt = s->cfg.worker_threads ? s->cfg.worker_threads : (max_n <= 160 ? 32 : max_n <= 1200 ? 64 : 128);
-    s->smem = smem_bytes_for(max_n, s->width / 8, 0);
+    s->csr_words = default_csr_words(max_n, s->cfg.stage_csr);
+    s->smem = smem_bytes_for(max_n, s->width / 8, s->csr_words);
     if (s->smem > (int)prop.sharedMemPerBlockOptin) {
         delete s;
         return VC_EINVAL;
@@ -413,7 +416,9 @@ int vc_server_create(const vc_config *cfg, size_t device_bytes_budget, int32_t m
     s->eb = entry_bytes_for(max_n, s->width / 8);
     s->depth = max_n + 3;  // MVC depth <= n + 1, PVC depth <= min(k, n) + 2
     s->slots = 4096;
-    s->cap = 4096;
+    // Worklist: the batch default, limited to an eighth of the budget.
+    s->cap = default_worklist_capacity(s->eb);
+    while (s->cap > 1024 && (size_t)s->cap * (size_t)s->eb > s->budget / 8) s->cap >>= 1;
     // Budget: half for the stacks (as many workers as fit), a quarter for the graph arena.
     const size_t per_worker = (size_t)s->depth * (size_t)s->eb;
     int64_t w = s->cfg.num_workers > 0 ? s->cfg.num_workers : (int64_t)prop.multiProcessorCount * per_sm;
