@@ -61,8 +61,23 @@ def dist_env():
 
 
 def workload(rank: int, count: int):
+    """Rank r solves its own graphs: streams r*4096 .. r*4096+count-1 (weak scaling, no overlap)."""
     from paper_2204_10402_gb300 import graphs as G
     return G.batch_gnp(count, first_seed=rank * NUM_GRAPHS)
+
+
+def combine(t_local: float, solves_local: int, device=None):
+    """Whole-job figures from every rank's own timing: the slowest rank's time and the sum of
+    the solves.  The ranks exchange only these two numbers (no data-path collective)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return t_local, solves_local
+    t = torch.tensor([t_local], dtype=torch.float64, device=device)
+    n = torch.tensor([solves_local], dtype=torch.int64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(n.item())
 
 
 def peaks():
@@ -256,13 +271,9 @@ def run_ours(a):
         vc.mvc_batch(b.vtx, b.edge, off_d, nbr_d, stream=stream, want_covers=False)
         call_ms.append(1000 * (time.perf_counter() - t0))
     t_local = sum(step_ms) / 1000.0
-    t_max = t_local
+    t_max, solves = combine(t_local, a.graphs * a.steps, dev)
     if world > 1:
-        tt = torch.tensor([t_local], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
         dist.barrier()
-    solves = a.graphs * a.steps * world
     value = solves / t_max
     nodes = sum(s["nodes_visited"] for s in stats)
 
@@ -306,6 +317,7 @@ def run_ours(a):
                        "variant": {"width": stats[0]["width"], "worker_threads": stats[0]["worker_threads"],
                                    "workers": stats[0]["workers"]}},
             "nodes_per_s": nodes * world / t_max,
+            "load_balance": load_balance(vc),
             "wrong_answers_vs_oracle": wrong,
             "batch_call_solves_per_s": a.graphs / (statistics.mean(call_ms) / 1000.0),
             "nodes_per_step": nodes / a.steps,
@@ -332,6 +344,17 @@ def run_ours(a):
         dist.barrier()
         dist.destroy_process_group()
     return out
+
+
+def load_balance(vc):
+    """Sec. V-C load measure for the last traversal: tree nodes per SM over the mean."""
+    per_sm = vc.last_sm_nodes().astype(np.float64)
+    per_sm = per_sm[per_sm > 0] if per_sm.any() else per_sm
+    if per_sm.size == 0:
+        return None
+    mean = per_sm.mean()
+    return {"sms": int(per_sm.size), "min_over_mean": float(per_sm.min() / mean),
+            "max_over_mean": float(per_sm.max() / mean)}
 
 
 def load_serve_pool():

@@ -130,15 +130,6 @@ int next_pow2(int x) {
     return p;
 }
 
-// Worker size by graph size: a warp for the small graphs, more threads per block as n grows
-// (Sec. IV-E: larger graphs want fewer, larger blocks).  The autotuner overrides this.
-int default_worker_threads(int n_max) {
-    if (n_max <= 160) return 32;
-    if (n_max <= 640) return 64;
-    if (n_max <= 2560) return 128;
-    return 256;
-}
-
 // Host description of one launch.
 struct Spec {
     std::vector<Problem> probs;
@@ -185,12 +176,12 @@ int run(Workspace &ws, const Spec &spec, const vc_config *cfg_in, cudaStream_t s
     const int n_max = std::max(spec.n_max, 1);
 
     // ---- variant: degree-array width and worker size ----
-    int width = cfg.width;
-    if (width == 0) width = n_max <= 32768 ? 16 : 32;
+    const LaunchDefaults tuned = tuned_defaults(n_max);
+    int width = cfg.width ? cfg.width : tuned.width;
     if (width != 16 && width != 32) return VC_EINVAL;
     if (width == 16 && n_max > 32768) return VC_EINVAL;
     const int wbytes = width / 8;
-    int wt = cfg.worker_threads ? cfg.worker_threads : default_worker_threads(n_max);
+    int wt = cfg.worker_threads ? cfg.worker_threads : tuned.worker_threads;
     if (!is_pow2(wt) || wt < 32 || wt > 512) return VC_EINVAL;
     // CSR staging in shared memory: when every graph's CSR size is known and small enough, each
     // worker keeps a copy of its current graph's CSR next to the degree array.
@@ -222,7 +213,7 @@ int run(Workspace &ws, const Spec &spec, const vc_config *cfg_in, cudaStream_t s
 
     // ---- worklist sizing (Sec. V-A explores 128K-512K entries, threshold 0.25-1.0 x size) ----
     int cap = cfg.worklist_capacity > 0 ? next_pow2(cfg.worklist_capacity) : default_worklist_capacity(eb);
-    float frac = cfg.donate_threshold > 0.f ? cfg.donate_threshold : 0.5f;
+    float frac = cfg.donate_threshold > 0.f ? cfg.donate_threshold : tuned.threshold;
     int threshold = (int)std::max<double>(0.0, std::min<double>(cap, (double)frac * cap));
     if (cfg.donate_threshold < 0.f) threshold = 0;  // never donate (stress setting)
 
@@ -548,9 +539,10 @@ int vc_reduce_node(const vc_graph *g, int32_t *deg, int32_t *S, int32_t *m, int3
     vc_config c;
     std::memset(&c, 0, sizeof(c));
     if (cfg) c = *cfg;
-    const int width = c.width ? c.width : (g->n <= 32768 ? 16 : 32);
+    const LaunchDefaults tuned = tuned_defaults(g->n);
+    const int width = c.width ? c.width : tuned.width;
     if ((width != 16 && width != 32) || (width == 16 && g->n > 32768)) return VC_EINVAL;
-    const int wt = c.worker_threads ? c.worker_threads : default_worker_threads(g->n);
+    const int wt = c.worker_threads ? c.worker_threads : tuned.worker_threads;
     const int smem = smem_bytes_for(g->n, width / 8);
     if (smem > ws->smem_optin) return VC_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;

@@ -67,8 +67,6 @@ int scratch_for_current_device(uint8_t **addr, int *sms) {
     return VC_OK;
 }
 
-int worker_threads_for(int n) { return n <= 160 ? 32 : 64; }
-
 }  // namespace
 }  // namespace vc
 
@@ -96,7 +94,7 @@ extern "C" int vc_mvc_noalloc(const vc_graph *g, const vc_config *cfg_in, void *
 
     // ---- variant (16-bit degree arrays; n <= 512 always fits) ----
     const int n = g->n;
-    const int wt = cfg.worker_threads ? cfg.worker_threads : worker_threads_for(n);
+    const int wt = cfg.worker_threads ? cfg.worker_threads : tuned_defaults(n).worker_threads;
     const int wbytes = 2;
     const int32_t csr_words = default_csr_words(n, cfg.stage_csr);
     const int smem = smem_bytes_for(n, wbytes, csr_words);

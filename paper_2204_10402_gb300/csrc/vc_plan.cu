@@ -87,12 +87,13 @@ int vc_plan_create_mvc_batch(int32_t G, const int32_t *vtx, const int32_t *edge,
     vc_plan *pl = new vc_plan();
     pl->G = G;
     pl->total_vertices = total_v;
-    pl->width = cfg.width ? cfg.width : (n_max <= 32768 ? 16 : 32);
+    const LaunchDefaults tuned = tuned_defaults(n_max);
+    pl->width = cfg.width ? cfg.width : tuned.width;
     if ((pl->width != 16 && pl->width != 32) || (pl->width == 16 && n_max > 32768)) {
         delete pl;
         return VC_EINVAL;
     }
-    pl->wt = cfg.worker_threads ? cfg.worker_threads : (n_max <= 160 ? 32 : n_max <= 640 ? 64 : n_max <= 2560 ? 128 : 256);
+    pl->wt = cfg.worker_threads ? cfg.worker_threads : tuned.worker_threads;
     const int32_t csr_words = default_csr_words(n_max, cfg.stage_csr);
     pl->smem = smem_bytes_for(n_max, pl->width / 8, csr_words);
     const Launchers &L = pl->width == 16 ? launchers_w16() : launchers_w32();
@@ -109,7 +110,7 @@ int vc_plan_create_mvc_batch(int32_t G, const int32_t *vtx, const int32_t *edge,
     else
         cap = default_worklist_capacity(pl->eb);
     pl->cap = cap;
-    const float frac = cfg.donate_threshold > 0.f ? cfg.donate_threshold : 0.5f;
+    const float frac = cfg.donate_threshold > 0.f ? cfg.donate_threshold : tuned.threshold;
     const int threshold = cfg.donate_threshold < 0.f ? 0 : std::max(0, std::min(cap, (int)(frac * cap)));
     const int64_t depth = (int64_t)n_max + 2;
 

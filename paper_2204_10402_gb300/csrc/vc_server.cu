@@ -395,12 +395,13 @@ int vc_server_create(const vc_config *cfg, size_t device_bytes_budget, int32_t m
     }
     s->max_n = max_n;
     s->budget = device_bytes_budget ? device_bytes_budget : (size_t(8) << 30);
-    s->width = s->cfg.width ? s->cfg.width : (max_n <= 32768 ? 16 : 32);
+    const LaunchDefaults tuned = tuned_defaults(max_n);
+    s->width = s->cfg.width ? s->cfg.width : tuned.width;
     if ((s->width != 16 && s->width != 32) || (s->width == 16 && max_n > 32768)) {
         delete s;
         return VC_EINVAL;
     }
-    s->wt = s->cfg.worker_threads ? s->cfg.worker_threads : (max_n <= 160 ? 32 : max_n <= 1200 ? 64 : 128);
+    s->wt = s->cfg.worker_threads ? s->cfg.worker_threads : tuned.worker_threads;
     s->csr_words = default_csr_words(max_n, s->cfg.stage_csr);
     s->smem = smem_bytes_for(max_n, s->width / 8, s->csr_words);
     if (s->smem > (int)prop.sharedMemPerBlockOptin) {
@@ -428,7 +429,7 @@ int vc_server_create(const vc_config *cfg, size_t device_bytes_budget, int32_t m
         return VC_ENOMEM;
     }
     s->workers = (int)w;
-    float frac = s->cfg.donate_threshold > 0.f ? s->cfg.donate_threshold : 0.5f;
+    float frac = s->cfg.donate_threshold > 0.f ? s->cfg.donate_threshold : tuned.threshold;
     s->threshold = std::max(1, (int)(frac * s->cap));
     if (s->cfg.worklist_capacity > 0) {
         int c = 1;

@@ -367,3 +367,47 @@ def test_batch_plan_graph_replay(vc):
     pb = G.pack([bad])
     with pytest.raises(vc.VCError):
         vc.BatchPlan(pb.vtx, pb.edge, pb.offsets, nb)
+
+
+def load_clique_golden():
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "planted_clique_mvc.txt")
+    rows = {}
+    for line in open(path):
+        if not line.startswith("#"):
+            n, c, m, size, nodes, secs = line.split()
+            rows[int(n)] = (int(c), int(m), int(size))
+    return rows
+
+
+def test_planted_clique_pvc_three_columns(vc):
+    # Table I's three PVC instances (k = min-1, min, min+1) on the planted-clique family.
+    g, _ = G.gnp_with_planted_clique(160, 0.05, 10, 0)
+    best, _, _ = oracle.mvc(g)
+    for k in (best - 1, best, best + 1):
+        a = vc.pvc(g.offsets, g.neighbors, k)
+        assert bool(a.value) == (k >= best)
+        if a.value:
+            check_cover(g, a.cover, a.cover_size)
+            assert a.cover_size <= k
+
+
+@pytest.mark.parametrize("n", [180, 200])
+def test_planted_clique_stored_answers(vc, n):
+    # Sizes the oracle needs minutes for (answers stored by tests/golden/make_clique_golden.py).
+    c, m, want = load_clique_golden()[n]
+    g, _ = G.gnp_with_planted_clique(n, 0.05, c, 0)
+    assert g.m == m
+    a = vc.mvc(g.offsets, g.neighbors)
+    assert a.value == want
+    check_cover(g, a.cover, want)
+    assert vc.pvc(g.offsets, g.neighbors, want - 1, want_cover=False).value == 0
+
+
+def test_per_sm_load_counts(vc):
+    # Sec. V-C load measure: every SM expands tree nodes and the counts add up to the total.
+    b = G.batch_gnp(1024)
+    sizes, _, st = vc.mvc_batch(b.vtx, b.edge, b.offsets, b.neighbors, want_covers=False)
+    per_sm = vc.last_sm_nodes()
+    assert per_sm.sum() == st["nodes_visited"]
+    assert (per_sm > 0).sum() >= 100
