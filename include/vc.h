@@ -76,6 +76,14 @@ typedef struct {
                                    n <= 1024, 1 = offsets and neighbour lists when they fit (fewer resident
                                    workers), -1 = nothing (all CSR reads through L1) */
     const volatile int32_t *cancel;  /* optional host-mapped or device flag; nonzero aborts with VC_ECANCELLED */
+    int32_t node_in_global;     /* placement of each worker's current node (degree array, marks, removal
+                                   list), Sec. IV-E's two kernel versions: 0 = shared memory when it fits,
+                                   else global memory; 1 = always global memory; -1 = shared memory only
+                                   (VC_EINVAL when it does not fit).  The global version keeps a private
+                                   region of about 2 x n x 4 bytes per worker and reads it through L2.
+                                   vc_mvc, vc_pvc, vc_mvc_batch, vc_greedy and vc_reduce_node honour it;
+                                   the server, the batch plan and vc_mvc_noalloc keep the node in shared
+                                   memory. */
 } vc_config;
 
 /* Counters of one call (all filled by the device except kernel_ms and the sizes). */
@@ -100,6 +108,8 @@ typedef struct {
     int64_t trace_ns[4];        /* builds with -DVC_TRACE: worker time waiting for work, in reduction rules and
                                    stop checks, branching, recording solutions (Sec. V-D breakdown); else 0 */
     int64_t idle_polls;         /* builds with -DVC_TRACE: idle-loop iterations; else 0 */
+    int32_t node_in_global;     /* 1 if the workers kept their current node in global memory */
+    int32_t stack_depth;        /* entries provisioned per local stack */
 } vc_stats;
 
 /* Minimum Vertex Cover (Sec. II-A, II-B, IV).

@@ -183,7 +183,10 @@ static_assert(kScTally + 2 * kTallySlots <= 40, "tally overlaps the argmax keys"
 // ------------------------------------------------------------------------------------------------
 // Worker
 // ------------------------------------------------------------------------------------------------
-template <typename W, int WT>
+// GM = false: the node lives in shared memory.  GM = true: the degree array, marks, dirty bits and
+// removal list live in a global-memory region of this worker (the header and scratch stay in
+// shared memory); their reads go through L2 (.cg) because the atomics that change them act there.
+template <typename W, int WT, bool GM = false>
 struct Worker {
     static constexpr int kWarps = WT / 32;
     EntryHeader *hdr;
@@ -204,15 +207,26 @@ struct Worker {
     int32_t cur_n;   // vertices of the current graph (for the debug checks)
     int32_t n_cap;   // shared-memory capacity in vertices
 
-    __device__ Worker(uint8_t *smem, int32_t n_max, int32_t csr_capacity = 0) {
+    __device__ Worker(uint8_t *smem, int32_t n_max, int32_t csr_capacity = 0, uint8_t *gstate = nullptr) {
         const int32_t eb = entry_bytes_for(n_max, (int32_t)sizeof(W));
-        hdr = reinterpret_cast<EntryHeader *>(smem);
-        d = reinterpret_cast<W *>(smem + 16);
-        marks = reinterpret_cast<uint32_t *>(smem + eb);
         const int32_t mark_bytes = pad16(((int64_t)n_max + 31) / 32 * 4);
-        dirty = reinterpret_cast<unsigned long long *>(smem + eb + mark_bytes);
-        list = reinterpret_cast<int32_t *>(smem + eb + mark_bytes + pad16(((int64_t)n_max + 31) / 32 * 8));
-        sc = list + pad16((int64_t)n_max * 4) / 4;
+        const int32_t dirty_bytes = pad16(((int64_t)n_max + 31) / 32 * 8);
+        hdr = reinterpret_cast<EntryHeader *>(smem);
+        if constexpr (GM) {
+            uint8_t *g = gstate;
+            d = reinterpret_cast<W *>(g);
+            g += pad16((int64_t)n_max * sizeof(W));
+            marks = reinterpret_cast<uint32_t *>(g);
+            dirty = reinterpret_cast<unsigned long long *>(g + mark_bytes);
+            list = reinterpret_cast<int32_t *>(g + mark_bytes + dirty_bytes);
+            sc = reinterpret_cast<int32_t *>(smem + 16);
+        } else {
+            d = reinterpret_cast<W *>(smem + 16);
+            marks = reinterpret_cast<uint32_t *>(smem + eb);
+            dirty = reinterpret_cast<unsigned long long *>(smem + eb + mark_bytes);
+            list = reinterpret_cast<int32_t *>(smem + eb + mark_bytes + dirty_bytes);
+            sc = list + pad16((int64_t)n_max * 4) / 4;
+        }
         keys = reinterpret_cast<unsigned long long *>(sc + kScKeys);
         tally = reinterpret_cast<unsigned long long *>(sc + kScTally);
         csr = sc + kScratchWords;
@@ -238,7 +252,18 @@ struct Worker {
         else return __syncthreads_or(p);
     }
 
-    __device__ __forceinline__ int deg(int v) const { return (int)d[v]; }
+    __device__ __forceinline__ int deg(int v) const {
+        if constexpr (GM) return (int)__ldcg(d + v);
+        else return (int)d[v];
+    }
+    __device__ __forceinline__ unsigned long long ld_dirty(int i) const {
+        if constexpr (GM) return __ldcg(dirty + i);
+        else return dirty[i];
+    }
+    __device__ __forceinline__ int ld_list(int i) const {
+        if constexpr (GM) return __ldcg(list + i);
+        else return list[i];
+    }
 
     // Atomic decrement of d[u] in shared memory.  For 16-bit entries the containing 32-bit word
     // is decremented in the right half; a live vertex with a removed neighbour has degree >= 1, so
@@ -252,7 +277,10 @@ struct Worker {
         }
     }
 
-    __device__ __forceinline__ bool marked(int u) const { return (marks[u >> 5] >> (u & 31)) & 1u; }
+    __device__ __forceinline__ bool marked(int u) const {
+        const uint32_t word = GM ? __ldcg(marks + (u >> 5)) : marks[u >> 5];
+        return (word >> (u & 31)) & 1u;
+    }
 
     // Choose u for S in the current pass (once, however many proposers).
     __device__ __forceinline__ void propose(int u) {
@@ -334,8 +362,17 @@ struct Worker {
     __device__ void load_entry(const uint8_t *src, int32_t bytes, int32_t n_max) {
         sync();  // no warp still reads the node being replaced
         const int4 *s = reinterpret_cast<const int4 *>(src);
-        int4 *t = reinterpret_cast<int4 *>(hdr);
-        for (int i = tid; i < bytes / 16; i += WT) t[i] = __ldcg(s + i);
+        if constexpr (GM) {
+            int4 *dg = reinterpret_cast<int4 *>(d);
+            for (int i = tid; i < bytes / 16; i += WT) {
+                const int4 v = __ldcg(s + i);
+                if (i == 0) *reinterpret_cast<int4 *>(hdr) = v;
+                else __stcg(dg + (i - 1), v);
+            }
+        } else {
+            int4 *t = reinterpret_cast<int4 *>(hdr);
+            for (int i = tid; i < bytes / 16; i += WT) t[i] = __ldcg(s + i);
+        }
         dirty_none(n_max);
         sync();
     }
@@ -343,9 +380,10 @@ struct Worker {
     // Copies the current node to global memory with its header's branch field set to `branch`.
     __device__ void store_entry(uint8_t *dst, int32_t bytes, int32_t branch) {
         int4 *t = reinterpret_cast<int4 *>(dst);
-        const int4 *s = reinterpret_cast<const int4 *>(hdr);
         for (int i = tid; i < bytes / 16; i += WT) {
-            int4 v = s[i];
+            int4 v;
+            if constexpr (GM) v = i == 0 ? *reinterpret_cast<const int4 *>(hdr) : __ldcg(reinterpret_cast<const int4 *>(d) + (i - 1));
+            else v = reinterpret_cast<const int4 *>(hdr)[i];
             if (i == 0) v.w = branch;
             __stcg(t + i, v);
         }
@@ -364,7 +402,7 @@ struct Worker {
         VC_CHECK(dbg, cnt >= 0 && cnt <= c.n, 3, cnt, cnt = 0);
         int edges = 0, words = 0;
         for (int i = warp; i < cnt; i += kWarps) {
-            const int u = list[i];
+            const int u = ld_list(i);
             VC_CHECK(dbg, u >= 0 && u < c.n, 4, u, continue);
             const int b = c.off[u], e = c.off[u + 1];
             VC_CHECK(dbg, b >= 0 && e >= b, 15, u, continue);
@@ -387,7 +425,7 @@ struct Worker {
         if (lane == 0 && words) atomicAdd(&tally[kTCsr], (unsigned long long)words);
         sync();
         for (int i = tid; i < cnt; i += WT) {
-            const int u = list[i];
+            const int u = ld_list(i);
             VC_CHECK(dbg, u >= 0 && u < c.n, 16, u, continue);
             d[u] = (W)-1;
             marks[u >> 5] = 0u;
@@ -473,7 +511,7 @@ struct Worker {
         bool proposed = false;
         int words = 0;
         for (int base = warp * 32; base < c.n; base += WT) {
-            const unsigned long long dw = dirty[base >> 5];
+            const unsigned long long dw = ld_dirty(base >> 5);
             const unsigned bits = (unsigned)dw;
             if (bits == 0u) continue;
             if (lane == 0) dirty[base >> 5] = dw & 0xffffffff00000000ull;
@@ -502,7 +540,7 @@ struct Worker {
         bool proposed = false;
         int words = 0;
         for (int base = warp * 32; base < c.n; base += WT) {
-            const unsigned long long dw = dirty[base >> 5];
+            const unsigned long long dw = ld_dirty(base >> 5);
             const unsigned bits = (unsigned)(dw >> 32);
             if (bits == 0u) continue;
             if (lane == 0) dirty[base >> 5] = dw & 0xffffffffull;

@@ -20,6 +20,7 @@ namespace {
 
 constexpr int kMaxDevices = 64;
 constexpr size_t kStackBudget = size_t(8) << 30;  // stacks beyond this size trigger a tighter depth
+constexpr int64_t kMinCappedDepth = 256;           // smallest per-worker depth worth a capped launch
 constexpr int64_t kDefaultIdleTimeoutNs = 20000000000ll;
 
 struct DevBuf {
@@ -32,7 +33,7 @@ struct Workspace {
     int device = -1;
     int sms = 0;
     int smem_optin = 0;
-    DevBuf csr_off, csr_adj, problems, adj_len, ctrl, cover, stacks, wl_slots, wl_seq, sm_nodes;
+    DevBuf csr_off, csr_adj, problems, adj_len, ctrl, cover, stacks, wl_slots, wl_seq, sm_nodes, gstate;
     void *pinned = nullptr;
     size_t pinned_cap = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -112,7 +113,7 @@ int workspace(Workspace **out) {
 
 void free_workspace(Workspace &ws) {
     DevBuf *bufs[] = {&ws.csr_off, &ws.csr_adj, &ws.problems, &ws.adj_len, &ws.ctrl, &ws.cover,
-                      &ws.stacks, &ws.wl_slots, &ws.wl_seq, &ws.sm_nodes};
+                      &ws.stacks, &ws.wl_slots, &ws.wl_seq, &ws.sm_nodes, &ws.gstate};
     for (DevBuf *b : bufs) {
         if (b->p) cudaFree(b->p);
         b->p = nullptr;
@@ -148,8 +149,8 @@ struct Result {
     std::vector<Problem> probs;
     Control ctrl;
     float kernel_ms = 0.f;
-    int workers = 0, wt = 0, width = 0;
-    bool csr_staged = false;
+    int workers = 0, wt = 0, width = 0, stack_depth = 0;
+    bool csr_staged = false, gm = false;
 };
 
 Problem make_problem(int64_t off_base, int64_t adj_base, int64_t cover_base, int32_t n, int32_t kind, int32_t k) {
@@ -203,8 +204,16 @@ int run(Workspace &ws, const Spec &spec, const vc_config *cfg_in, cudaStream_t s
         csr_words = 0;
         smem = smem_bytes_for(n_max, wbytes, 0);
     }
+    // Node placement (Sec. IV-E): shared memory when it fits, else the global-memory version.
+    const bool gm = cfg.node_in_global > 0 || (cfg.node_in_global == 0 && smem > ws.smem_optin);
+    if (gm) {
+        csr_words = default_csr_words(n_max, cfg.stage_csr);
+        if (known && cfg.stage_csr > 0 && csr_need > 0 && smem_bytes_gm((int32_t)csr_need) <= ws.smem_optin)
+            csr_words = (int32_t)csr_need;
+        smem = smem_bytes_gm(csr_words);
+    }
     if (smem > ws.smem_optin) return VC_EINVAL;  // graph too large for a shared-memory degree array
-    const Launchers &L = width == 16 ? launchers_w16() : launchers_w32();
+    const Launchers &L = launchers(width, gm);
     int per_sm = 0;
     VC_RC(L.occupancy(wt, smem, &per_sm));
     if (per_sm <= 0) return VC_EINVAL;
@@ -274,6 +283,11 @@ int run(Workspace &ws, const Spec &spec, const vc_config *cfg_in, cudaStream_t s
     P.idle_timeout_ns = cfg.idle_timeout_ns > 0 ? cfg.idle_timeout_ns : kDefaultIdleTimeoutNs;
     P.cancel = cfg.cancel;
     P.sm_nodes = static_cast<unsigned long long *>(ws.sm_nodes.p);
+    if (gm) {
+        P.gstate_bytes = gstate_bytes_for(n_max, wbytes);
+        VC_RC(grow(ws.gstate, (size_t)workers * (size_t)P.gstate_bytes));
+        P.gstate = static_cast<uint8_t *>(ws.gstate.p);
+    }
 
     if (!cfg.skip_validation)
         VC_RC(launch_validate(d_off, d_adj, d_probs, static_cast<const int64_t *>(ws.adj_len.p), G,
@@ -291,7 +305,12 @@ int run(Workspace &ws, const Spec &spec, const vc_config *cfg_in, cudaStream_t s
                 d2 = std::max<int64_t>(d2, p.kind == kMVC ? (int64_t)p.greedy + 2 : (int64_t)std::min(p.k, p.n) + 3);
             }
             depth = std::min(depth, d2);
-            while (workers > ws.sms && (size_t)workers * (size_t)depth * (size_t)eb > kStackBudget) workers /= 2;
+            // Still over the budget (large graphs): halve the workers while each would get fewer
+            // than kMinCappedDepth entries, then cap the depth to what fits; a search that goes
+            // deeper than the cap stops with VC_ESTACK.
+            auto fit = [&] { return (int64_t)(kStackBudget / ((size_t)workers * (size_t)eb)); };
+            while (workers > ws.sms && depth > fit() && fit() < kMinCappedDepth) workers /= 2;
+            if (depth > fit()) depth = std::max<int64_t>(fit(), 2);
         }
         P.stack_depth = (int32_t)depth;
         VC_RC(grow(ws.stacks, (size_t)workers * (size_t)depth * (size_t)eb));
@@ -334,6 +353,8 @@ int run(Workspace &ws, const Spec &spec, const vc_config *cfg_in, cudaStream_t s
     res.wt = wt;
     res.width = width;
     res.csr_staged = csr_words > 0;
+    res.gm = gm;
+    res.stack_depth = spec.search ? (int)depth : 0;
     return h_ctrl->status;
 }
 
@@ -356,6 +377,8 @@ void fill_stats(vc_stats *st, const Result &r, double total_ms, int32_t greedy) 
     st->worker_threads = r.wt;
     st->width = r.width;
     st->csr_staged = r.csr_staged ? 1 : 0;
+    st->node_in_global = r.gm ? 1 : 0;
+    st->stack_depth = r.stack_depth;
     st->status = r.ctrl.status;
     st->kernel_ms = r.kernel_ms;
     st->total_ms = (float)total_ms;
@@ -543,7 +566,9 @@ int vc_reduce_node(const vc_graph *g, int32_t *deg, int32_t *S, int32_t *m, int3
     const int width = c.width ? c.width : tuned.width;
     if ((width != 16 && width != 32) || (width == 16 && g->n > 32768)) return VC_EINVAL;
     const int wt = c.worker_threads ? c.worker_threads : tuned.worker_threads;
-    const int smem = smem_bytes_for(g->n, width / 8);
+    int smem = smem_bytes_for(g->n, width / 8);
+    const bool gm = c.node_in_global > 0 || (c.node_in_global == 0 && smem > ws->smem_optin);
+    if (gm) smem = smem_bytes_gm(0);
     if (smem > ws->smem_optin) return VC_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t len = g->on_device ? -1 : g->offsets[g->n];
@@ -596,7 +621,12 @@ int vc_reduce_node(const vc_graph *g, int32_t *deg, int32_t *S, int32_t *m, int3
     R.branch = branch;
     R.deg = d_deg;
     R.io = d_io;
-    const Launchers &L = width == 16 ? launchers_w16() : launchers_w32();
+    R.gstate = nullptr;
+    if (gm) {
+        VC_RC(grow(ws->gstate, (size_t)gstate_bytes_for(g->n, width / 8)));
+        R.gstate = static_cast<uint8_t *>(ws->gstate.p);
+    }
+    const Launchers &L = launchers(width, gm);
     VC_RC(L.reduce(wt, smem, s, R));
     VC_CK(cudaMemcpyAsync(deg, d_deg, deg_bytes, g->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
     VC_CK(cudaMemcpyAsync(h_io, d_io, 3 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));

@@ -101,6 +101,8 @@ struct Params {
     int32_t wl_capacity;
     int32_t wl_threshold;    // donate while fewer than this many entries wait in the worklist
     int32_t csr_words;       // shared-memory CSR staging capacity in int32 words (0 = read the CSR from global)
+    uint8_t *gstate;         // global-memory node state, gstate_bytes per worker (global-state kernels)
+    int32_t gstate_bytes;
     int64_t idle_timeout_ns;
     const volatile int32_t *cancel;
     unsigned long long *sm_nodes;  // per-SM node counters
@@ -126,6 +128,7 @@ struct ReduceParams {
     int32_t branch;   // -1: reduce as given; v >= 0: put v into S first; -2-v: put N(v) into S first
     int32_t *deg;     // n entries, in/out (device)
     int32_t *io;      // [0] = S, [1] = m, [2] = pruned (out)
+    uint8_t *gstate;  // global-state kernels: one worker's node state
 };
 
 #ifdef __CUDACC__
@@ -182,6 +185,20 @@ VC_HD inline int32_t default_worklist_capacity(int32_t entry_bytes) {
     int64_t cap = 262144;
     while (cap > 1024 && cap * (int64_t)entry_bytes > (int64_t(1) << 30)) cap >>= 1;
     return (int32_t)cap;
+}
+
+// Global-state variant (Sec. IV-E: the paper's kernel version that keeps the current intermediate
+// graph in global memory): shared memory keeps only the 16-byte header, the scratch words and any
+// staged CSR; the degree array, marks, dirty bits and removal list live in a per-worker region.
+VC_HD inline int32_t smem_bytes_gm(int32_t csr_words) {
+    return 16 + kScratchWords * 4 + pad16((int64_t)csr_words * 4);
+}
+VC_HD inline int32_t gstate_bytes_for(int32_t n_max, int32_t width_bytes) {
+    int64_t b = pad16((int64_t)n_max * width_bytes);
+    b += pad16(((int64_t)n_max + 31) / 32 * 4);
+    b += pad16(((int64_t)n_max + 31) / 32 * 8);
+    b += pad16((int64_t)n_max * 4);
+    return (int32_t)b;
 }
 
 // Shared-memory CSR staging by default: the offsets (n+1 ints) of graphs with up to

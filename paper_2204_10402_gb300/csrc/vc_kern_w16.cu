@@ -1,10 +1,10 @@
-// 16-bit degree-array instances of the kernels (graphs with n <= 32768).
+// 16-bit degree-array instances of the kernels, node in shared memory (graphs with n <= 32768).
 #include "vc_launch_impl.cuh"
 
 namespace vc {
 const Launchers &launchers_w16() {
-    static const Launchers L = {&LaunchImpl<int16_t>::greedy, &LaunchImpl<int16_t>::traverse,
-                                &LaunchImpl<int16_t>::reduce, &LaunchImpl<int16_t>::occupancy};
+    using I = LaunchImpl<int16_t, false>;
+    static const Launchers L = {&I::greedy, &I::traverse, &I::reduce, &I::occupancy};
     return L;
 }
 }  // namespace vc

@@ -1,10 +1,10 @@
-// 32-bit degree-array instances of the kernels.
+// 32-bit degree-array instances of the kernels, node in shared memory.
 #include "vc_launch_impl.cuh"
 
 namespace vc {
 const Launchers &launchers_w32() {
-    static const Launchers L = {&LaunchImpl<int32_t>::greedy, &LaunchImpl<int32_t>::traverse,
-                                &LaunchImpl<int32_t>::reduce, &LaunchImpl<int32_t>::occupancy};
+    using I = LaunchImpl<int32_t, false>;
+    static const Launchers L = {&I::greedy, &I::traverse, &I::reduce, &I::occupancy};
     return L;
 }
 }  // namespace vc

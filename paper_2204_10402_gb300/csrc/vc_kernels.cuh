@@ -33,8 +33,8 @@ __global__ void init_worklist_kernel(uint32_t *seq, int32_t capacity, Control *c
 // PVC found flag when the greedy cover already fits) in its record.  Returns whether a search is
 // still needed (uniform across the block).
 // ------------------------------------------------------------------------------------------------
-template <typename W, int WT>
-__device__ bool greedy_solve(const Params &P, Worker<W, WT> &w, Ctx &c) {
+template <typename W, int WT, bool GM>
+__device__ bool greedy_solve(const Params &P, Worker<W, WT, GM> &w, Ctx &c) {
     w.cur_n = c.n;
     if (c.n == 0) {
         w.sync();
@@ -73,10 +73,10 @@ __device__ bool greedy_solve(const Params &P, Worker<W, WT> &w, Ctx &c) {
     return c.kind == kMVC ? S > 0 : (c.k >= 0 && S > c.k);
 }
 
-template <typename W, int WT>
+template <typename W, int WT, bool GM>
 __global__ void __launch_bounds__(WT) greedy_kernel(Params P) {
     extern __shared__ __align__(16) uint8_t smem[];
-    Worker<W, WT> w(smem, P.n_max, P.csr_words);
+    Worker<W, WT, GM> w(smem, P.n_max, P.csr_words, P.gstate + (size_t)blockIdx.x * (size_t)P.gstate_bytes);
     w.init_scratch(P.n_max);
     if (w.tid == 0) w.sc[kScB0] = ld_relaxed(&P.ctrl->status);
     w.sync();
@@ -184,8 +184,8 @@ __device__ __forceinline__ bool cover_lock(const Params &P, Problem *pr) {
 // An edgeless node passed the stop check: MVC lowers best (atomicMin) and, if it still holds the
 // smallest size under the cover lock, writes its cover; PVC raises the found flag and the first
 // worker to raise it writes the cover (Sec. IV-A).
-template <typename W, int WT>
-__device__ void record_solution(const Params &P, Worker<W, WT> &w, const Ctx &c) {
+template <typename W, int WT, bool GM>
+__device__ void record_solution(const Params &P, Worker<W, WT, GM> &w, const Ctx &c) {
     const int32_t S = w.hdr->S;
     bool locked = false, write = false;
     if (w.tid == 0) {
@@ -278,8 +278,8 @@ __device__ __forceinline__ int serve_wait(const Params &P, int &arg) {
 // worklist; idles with a growing sleep while other workers still hold work.  Returns 0 (stop),
 // 1 (a root is loaded) or 2 (a worklist entry is loaded).  Sec. IV-C: the search is over when
 // the worklist is empty and no worker holds work, i.e. when no work unit is left.
-template <typename W, int WT>
-__device__ int acquire(const Params &P, Worker<W, WT> &w) {
+template <typename W, int WT, bool GM>
+__device__ int acquire(const Params &P, Worker<W, WT, GM> &w) {
     Control *ctrl = P.ctrl;
     if (w.tid == 0) {
         int result = 0, arg = 0;
@@ -362,10 +362,10 @@ __device__ int acquire(const Params &P, Worker<W, WT> &w) {
 // ------------------------------------------------------------------------------------------------
 // At most 64 registers per thread, so every worker size keeps 2048 threads resident per SM
 // (measured: the uncapped build used 72 registers, fit 28 one-warp blocks per SM and ran 4 % slower).
-template <typename W, int WT>
+template <typename W, int WT, bool GM>
 __global__ void __launch_bounds__(WT, 1024 / WT) traverse_kernel(Params P) {
     extern __shared__ __align__(16) uint8_t smem[];
-    Worker<W, WT> w(smem, P.n_max, P.csr_words);
+    Worker<W, WT, GM> w(smem, P.n_max, P.csr_words, P.gstate + (size_t)blockIdx.x * (size_t)P.gstate_bytes);
     w.init_scratch(P.n_max);
     Control *ctrl = P.ctrl;
     w.dbg = ctrl;
@@ -531,10 +531,10 @@ __global__ void __launch_bounds__(WT, 1024 / WT) traverse_kernel(Params P) {
 // One node's reduction (tests): reads an int32 degree array, reduces it to the fixpoint in shared
 // memory (no early exit, like the oracle), writes it back with |S|, m and the stop verdict.
 // ------------------------------------------------------------------------------------------------
-template <typename W, int WT>
+template <typename W, int WT, bool GM>
 __global__ void __launch_bounds__(WT) reduce_node_kernel(ReduceParams R) {
     extern __shared__ __align__(16) uint8_t smem[];
-    Worker<W, WT> w(smem, R.n);
+    Worker<W, WT, GM> w(smem, R.n, 0, R.gstate);
     w.init_scratch(R.n);
     Ctx c;
     c.off = R.offsets;
@@ -545,7 +545,7 @@ __global__ void __launch_bounds__(WT) reduce_node_kernel(ReduceParams R) {
     c.kind = R.problem;
     c.k = R.bound;
     c.index = 0;
-    for (int v = w.tid; v < R.n; v += WT) w.d[v] = (W)R.deg[v];
+    for (int v = w.tid; v < R.n; v += WT) w.d[v] = (W)R.deg[v];  // plain stores; read after sync()
     if (R.branch == -1) w.dirty_all(R.n);  // a state from outside: every vertex is looked at
     if (w.tid == 0) {
         w.hdr->problem = 0;

@@ -1,5 +1,6 @@
 // vc_launch.h - host-side entry points into the templated kernels, one set per degree-array
-// width (instantiated in vc_kern_w16.cu and vc_kern_w32.cu).
+// width and node placement (vc_kern_w16.cu, vc_kern_w32.cu: node in shared memory;
+// vc_kern_w16_gm.cu, vc_kern_w32_gm.cu: node in global memory).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -18,6 +19,12 @@ struct Launchers {
 
 const Launchers &launchers_w16();
 const Launchers &launchers_w32();
+const Launchers &launchers_w16_gm();
+const Launchers &launchers_w32_gm();
+inline const Launchers &launchers(int width, bool gm) {
+    if (gm) return width == 16 ? launchers_w16_gm() : launchers_w32_gm();
+    return width == 16 ? launchers_w16() : launchers_w32();
+}
 
 // Non-templated kernels (vc_common.cu).
 int launch_validate(const int32_t *offsets, const int32_t *neighbors, const Problem *probs,

@@ -1,5 +1,5 @@
-// vc_launch_impl.cuh - instantiates the kernels of one degree-array width W for every supported
-// worker size and exposes them through a Launchers table.
+// vc_launch_impl.cuh - instantiates the kernels of one degree-array width W and one node placement
+// (GM: shared or global memory) for every supported worker size, behind a Launchers table.
 #pragma once
 
 #include "vc_kernels.cuh"
@@ -28,33 +28,33 @@ static inline int launch_status() { return cudaPeekAtLastError() == cudaSuccess 
         default: return VC_EINVAL;                          \
     }
 
-template <typename W>
+template <typename W, bool GM>
 struct LaunchImpl {
     static int greedy(int wt, int grid, int smem, cudaStream_t s, const Params &P) {
         VC_WT_SWITCH(wt, {
-            if (int rc = prepare(greedy_kernel<W, WT>, smem)) return rc;
-            greedy_kernel<W, WT><<<grid, WT, smem, s>>>(P);
+            if (int rc = prepare(greedy_kernel<W, WT, GM>, smem)) return rc;
+            greedy_kernel<W, WT, GM><<<grid, WT, smem, s>>>(P);
         });
         return launch_status();
     }
     static int traverse(int wt, int grid, int smem, cudaStream_t s, const Params &P) {
         VC_WT_SWITCH(wt, {
-            if (int rc = prepare(traverse_kernel<W, WT>, smem)) return rc;
-            traverse_kernel<W, WT><<<grid, WT, smem, s>>>(P);
+            if (int rc = prepare(traverse_kernel<W, WT, GM>, smem)) return rc;
+            traverse_kernel<W, WT, GM><<<grid, WT, smem, s>>>(P);
         });
         return launch_status();
     }
     static int reduce(int wt, int smem, cudaStream_t s, const ReduceParams &R) {
         VC_WT_SWITCH(wt, {
-            if (int rc = prepare(reduce_node_kernel<W, WT>, smem)) return rc;
-            reduce_node_kernel<W, WT><<<1, WT, smem, s>>>(R);
+            if (int rc = prepare(reduce_node_kernel<W, WT, GM>, smem)) return rc;
+            reduce_node_kernel<W, WT, GM><<<1, WT, smem, s>>>(R);
         });
         return launch_status();
     }
     static int occupancy(int wt, int smem, int *blocks) {
         VC_WT_SWITCH(wt, {
-            if (int rc = prepare(traverse_kernel<W, WT>, smem)) return rc;
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, traverse_kernel<W, WT>, WT, smem) !=
+            if (int rc = prepare(traverse_kernel<W, WT, GM>, smem)) return rc;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, traverse_kernel<W, WT, GM>, WT, smem) !=
                 cudaSuccess)
                 return VC_ECUDA;
         });

@@ -85,6 +85,7 @@ extern "C" int vc_mvc_noalloc(const vc_graph *g, const vc_config *cfg_in, void *
     vc_config cfg;
     std::memset(&cfg, 0, sizeof(cfg));
     if (cfg_in) cfg = *cfg_in;
+    if (cfg.node_in_global > 0) return VC_EINVAL;  // the node stays in shared memory here
     cudaStream_t s = (cudaStream_t)stream;
 
     std::lock_guard<std::mutex> lock(g_noalloc_mu);

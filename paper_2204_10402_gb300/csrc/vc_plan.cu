@@ -56,6 +56,7 @@ int vc_plan_create_mvc_batch(int32_t G, const int32_t *vtx, const int32_t *edge,
     vc_config cfg;
     std::memset(&cfg, 0, sizeof(cfg));
     if (cfg_in) cfg = *cfg_in;
+    if (cfg.node_in_global > 0) return VC_EINVAL;  // plans keep the node in shared memory
     int dev = 0;
     cudaDeviceProp prop;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return VC_ECUDA;

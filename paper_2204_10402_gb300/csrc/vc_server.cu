@@ -384,6 +384,10 @@ int vc_server_create(const vc_config *cfg, size_t device_bytes_budget, int32_t m
     vc_server *s = new vc_server();
     std::memset(&s->cfg, 0, sizeof(s->cfg));
     if (cfg) s->cfg = *cfg;
+    if (s->cfg.node_in_global > 0) {  // the server keeps the node in shared memory
+        delete s;
+        return VC_EINVAL;
+    }
     if (cudaGetDevice(&s->device) != cudaSuccess) {
         delete s;
         return VC_ECUDA;

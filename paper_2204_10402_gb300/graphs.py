@@ -284,6 +284,22 @@ def disjoint_union(a: CSR, b: CSR) -> CSR:
     return csr_from_edges(a.n + b.n, np.concatenate([ua, ub + a.n]), np.concatenate([va, vb + a.n]))
 
 
+def random_tree_parents(n: int, seed: int) -> np.ndarray:
+    """Random recursive tree: vertex i >= 1 hangs below a uniform earlier vertex; parent[0] = -1."""
+    parent = np.full(n, -1, dtype=np.int64)
+    if n > 1:
+        u = uniform01(seed, n - 1)
+        i = np.arange(1, n)
+        parent[1:] = np.minimum((u * i).astype(np.int64), i - 1)
+    return parent
+
+
+def random_tree(n: int, seed: int) -> CSR:
+    parent = random_tree_parents(n, seed)
+    i = np.arange(1, n)
+    return csr_from_edges(n, parent[1:], i)
+
+
 def random_bipartite(a: int, b: int, p: float, seed: int) -> CSR:
     """Bipartite graph with sides 0..a-1 and a..a+b-1; each cross pair is an edge iff its draw < p."""
     u = uniform01(seed, a * b).reshape(a, b)

@@ -6,6 +6,8 @@
 - complement_clique_mvc: the complement of a minimum cover is a maximum independent set, i.e. a
   maximum clique of the complement graph; the clique comes from networkx.
 - maximal_matching_size: any maximal matching is a lower bound on the cover size.
+- tree_mvc: the textbook dynamic programme over a rooted tree (each vertex either in the cover,
+  or out of it with all its children in).
 - load_rule_cases: parses tests/golden/rules.txt.
 """
 from __future__ import annotations
@@ -51,6 +53,20 @@ def complement_clique_mvc(g) -> int:
     h.remove_edges_from(zip(u.tolist(), v.tolist()))
     clique, _ = nx.max_weight_clique(h, weight=None)
     return g.n - len(clique)
+
+
+def tree_mvc(parent: np.ndarray) -> int:
+    """Minimum cover of the forest given by parent[] (parent[v] < v, roots have -1)."""
+    n = len(parent)
+    take = np.ones(n, dtype=np.int64)   # v in the cover: 1 + sum over children of the better choice
+    skip = np.zeros(n, dtype=np.int64)  # v not in the cover: every child is in it
+    for v in range(n - 1, -1, -1):
+        p = int(parent[v])
+        if p >= 0:
+            take[p] += min(take[v], skip[v])
+            skip[p] += take[v]
+    roots = np.nonzero(parent < 0)[0]
+    return int(sum(min(take[r], skip[r]) for r in roots))
 
 
 def maximal_matching_size(g) -> int:

@@ -110,6 +110,19 @@ def test_disjoint_union_additivity():
     assert oracle.mvc(total)[0] == want
 
 
+@pytest.mark.parametrize("seed", range(6))
+def test_tree_dynamic_programme(seed):
+    # Trees: the rules alone solve them, and the answer has a textbook dynamic programme.
+    for n in (1, 2, 9, 40, 300):
+        parent = G.random_tree_parents(n, seed * 1000 + n)
+        g = G.random_tree(n, seed * 1000 + n)
+        want = pins.tree_mvc(parent)
+        if n <= 20:
+            assert pins.brute_force_mvc(g) == want
+        assert oracle.mvc(g)[0] == want
+        assert oracle.greedy(g)[0] == want
+
+
 def test_greedy_bounds_and_covers():
     for g in random_small_graphs(40, seed0=3000) + [G.gnp(60, 0.1, 0), G.gnp(120, 0.05, 4)]:
         gs, gc = oracle.greedy(g)
