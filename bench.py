@@ -89,6 +89,51 @@ def peaks():
     return 6800.0, "fallback"
 
 
+def measured_traffic_per_node():
+    """DRAM bytes per tree node of the traversal kernel from the committed ncu summary, or None
+    when the kernel sources changed since that capture (the summary records their hash)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traverse_kernel_batch_gnp.md")
+    if not os.path.exists(path):
+        return None
+    rec = {}
+    for line in open(path):
+        if ":" in line and line.split(":")[0] in ("kernel_source_hash", "dram_bytes_per_tree_node"):
+            k, v = line.split(":", 1)
+            rec[k] = v.strip()
+    csrc = os.path.join(ROOT, "paper_2204_10402_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(f.encode())
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(fh.read())
+    if rec.get("kernel_source_hash") != h.hexdigest()[:16] or "dram_bytes_per_tree_node" not in rec:
+        return None
+    return float(rec["dram_bytes_per_tree_node"])
+
+
+def l2_copy_peak(dev) -> float:
+    """GB/s of a device copy whose 64 MiB working set stays in L2 (read + write bytes), best of 5
+    timings of 20 back-to-back copies."""
+    import torch
+    a = torch.empty(8 << 20, dtype=torch.float32, device=dev)
+    b = torch.empty_like(a)
+    a.fill_(1.0)
+    for _ in range(5):
+        b.copy_(a)
+    best = float("inf")
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(20):
+            b.copy_(a)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1) / 20)
+    return 2 * a.numel() * 4 / (best * 1e-3) / 1e9
+
+
 # ------------------------------------------------------------------------------------------------
 # CPU oracle legs (test infrastructure, timed as the reported baseline)
 # ------------------------------------------------------------------------------------------------
@@ -301,10 +346,18 @@ def run_ours(a):
         alg_bytes = [s["entry_bytes_moved"] + 4 * s["csr_words"] for s in stats]
         ach = [bb / (km * 1e-3) / 1e9 for bb, km in zip(alg_bytes, kernel_ms) if km > 0]
         achieved = statistics.mean(ach) if ach else 0.0
+        per_node = measured_traffic_per_node()
+        nodes_per_launch = statistics.mean(s["nodes_visited"] for s in stats)
+        l2_peak = l2_copy_peak(dev)
         roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                    "frac": achieved / hbm, "traffic": None, "peak_kind": peak_kind,
-                    "kernel": "traverse_kernel", "kernel_ms_mean": statistics.mean(kernel_ms),
-                    "alg_bytes_per_launch": statistics.mean(alg_bytes)}
+                    "frac": achieved / hbm,
+                    "traffic": per_node * nodes_per_launch if per_node is not None else None,
+                    "traffic_note": "ncu dram bytes per tree node (512-graph capture) x nodes of this launch",
+                    "peak_kind": peak_kind, "kernel": "traverse_kernel",
+                    "kernel_ms_mean": statistics.mean(kernel_ms),
+                    "alg_bytes_per_launch": statistics.mean(alg_bytes),
+                    "l2": {"peak_probe_gbs": l2_peak, "frac": achieved / l2_peak,
+                           "probe": "64 MiB device copy, L2-resident, read+write bytes"}}
         line = {
             "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": 1000 * t_max / a.steps, "higher_is_better": True,

@@ -7,6 +7,8 @@ Knobs (all fields of vc_config, include/vc.h):
   worklist_capacity   worklist entries (Sec. V-A)
   stage_csr           shared-memory placement of the current graph: offsets (0), offsets and
                       neighbour lists (1), nothing (-1)
+  node_in_global      placement of the current node (Sec. IV-E's two kernel versions): shared
+                      memory when it fits (0) or global memory (1)
 
 Search: coordinate descent from the library's defaults -- each knob in turn is set to the value
 with the lowest measured traversal time while the others stay fixed; two sweeps.  Results are
@@ -27,6 +29,7 @@ SPACE = {
     "donate_threshold": (0.25, 0.5, 1.0),
     "worklist_capacity": (16384, 65536, 262144),
     "stage_csr": (0, 1, -1),
+    "node_in_global": (0, 1),
 }
 
 
