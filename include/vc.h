@@ -84,6 +84,13 @@ typedef struct {
                                    vc_mvc, vc_pvc, vc_mvc_batch, vc_greedy and vc_reduce_node honour it;
                                    the server, the batch plan and vc_mvc_noalloc keep the node in shared
                                    memory. */
+    int32_t bit_rows;           /* adjacency lookups of one-warp, shared-memory workers on graphs of at most
+                                   128 vertices: 0 = bit rows of the adjacency matrix in shared memory when
+                                   the launch qualifies, else CSR walks; 1 = bit rows (VC_EINVAL when the
+                                   launch does not qualify); -1 = CSR walks.  Same answers and reduced
+                                   degree arrays either way.  vc_mvc, vc_pvc, vc_mvc_batch, vc_greedy,
+                                   vc_reduce_node and the batch plan honour it; the server and
+                                   vc_mvc_noalloc walk the CSR. */
 } vc_config;
 
 /* Counters of one call (all filled by the device except kernel_ms and the sizes). */
@@ -110,6 +117,14 @@ typedef struct {
     int64_t idle_polls;         /* builds with -DVC_TRACE: idle-loop iterations; else 0 */
     int32_t node_in_global;     /* 1 if the workers kept their current node in global memory */
     int32_t stack_depth;        /* entries provisioned per local stack */
+    int32_t bit_rows;           /* words per adjacency bit row the workers used (0: CSR walks) */
+    int64_t trace_cycles[16];   /* builds with -DVC_TRACE: SM cycles of each worker's first thread, summed
+                                   over workers, in: [0] per-node snapshot, [1] degree-one, [2] degree-two-
+                                   triangle and [3] high-degree pass scans, [4] removals applied by the
+                                   passes, [5] stop checks, [6] argmax, [7] donate or push, [8] the "v"
+                                   child, [9] stack pops, [10] N(v) children applied by their takers,
+                                   [11] acquiring work, [12] solutions; [13]-[15] the number of degree-one,
+                                   triangle and high-degree passes; else 0 */
 } vc_stats;
 
 /* Minimum Vertex Cover (Sec. II-A, II-B, IV).

@@ -50,7 +50,7 @@ class Config(ctypes.Structure):
                 ("width", ctypes.c_int32), ("worklist_capacity", ctypes.c_int32),
                 ("donate_threshold", ctypes.c_float), ("idle_timeout_ns", ctypes.c_int64),
                 ("skip_validation", ctypes.c_int32), ("stage_csr", ctypes.c_int32),
-                ("cancel", ctypes.c_void_p), ("node_in_global", ctypes.c_int32)]
+                ("cancel", ctypes.c_void_p), ("node_in_global", ctypes.c_int32), ("bit_rows", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -63,11 +63,13 @@ class Stats(ctypes.Structure):
                 ("status", ctypes.c_int32),
                 ("kernel_ms", ctypes.c_float), ("total_ms", ctypes.c_float),
                 ("trace_ns", ctypes.c_int64 * 4), ("idle_polls", ctypes.c_int64),
-                ("node_in_global", ctypes.c_int32), ("stack_depth", ctypes.c_int32)]
+                ("node_in_global", ctypes.c_int32), ("stack_depth", ctypes.c_int32),
+                ("bit_rows", ctypes.c_int32), ("trace_cycles", ctypes.c_int64 * 16)]
 
     def as_dict(self) -> dict:
         d = {name: getattr(self, name) for name, _ in self._fields_}
         d["trace_ns"] = list(self.trace_ns)
+        d["trace_cycles"] = list(self.trace_cycles)
         return d
 
 

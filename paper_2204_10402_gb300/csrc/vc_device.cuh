@@ -11,6 +11,9 @@
 //   [sc]     kScratchWords int32: pass counters, broadcasts, per-warp reduction keys
 //   [csr]    optional copy of the current graph's CSR (offsets, then neighbours), so that the
 //            adjacency walks of the rules and branches cost shared-memory latency
+//   [rows]   bit-row workers (NW > 0) only: the live-vertex mask and the pass's chosen set (NW
+//            words each, 16 B apart), then the current graph's adjacency as one NW-word bit row
+//            per vertex (a read-only copy of the CSR, like [csr])
 //
 // Degree-array semantics (Sec. IV-B): d[v] >= 0 is v's degree in G - S, d[v] = -1 means v is in S.
 // W is int16_t or int32_t; -1 is the sentinel at both widths.
@@ -36,7 +39,7 @@ enum : int {
     kScB3 = 5,
     kScB4 = 6,
     kScB5 = 7,
-    kScKeys = 48,   // 32 x u64 per-warp argmax keys (words 48..111)
+    kScKeys = 48,   // 16 x u64 per-warp argmax keys (words 48..79)
 };
 
 // ------------------------------------------------------------------------------------------------
@@ -166,7 +169,51 @@ enum TallySlot : int {
 constexpr int kScTally = 8;  // first scratch word of the tally (8-byte aligned, 16 slots)
 static_assert(kScTally + 2 * kTallySlots <= 40, "tally overlaps the argmax keys");
 
+// Finer breakdown in VC_TRACE builds: SM cycles (clock64) of thread 0 per activity, plus pass
+// counts, accumulated in scratch words kScProf.. and summed over workers at the end.
+enum ProfSlot {
+    kPHeader = 0,  // per-node snapshot of best / found / status
+    kPDeg1,        // degree-one pass scans (incl. their closing vote)
+    kPTri,         // degree-two-triangle pass scans
+    kPHigh,        // high-degree pass scans
+    kPApply,       // removals applied by rule passes
+    kPStop,        // |S| and m > t^2 checks
+    kPArgmax,      // argmax
+    kPStore,       // donate (reserve + entry copy + publish) or push
+    kPTakeV,       // the "v" child: v into S
+    kPPop,         // local stack pop (entry copy)
+    kPTakeN,       // lazily stored N(v) child applied by its taker
+    kPAcquire,     // roots and worklist (incl. idle waiting)
+    kPSolution,    // solution capture
+    kPDeg1Count,   // number of degree-one passes
+    kPTriCount,    // number of degree-two-triangle passes
+    kPHighCount,   // number of high-degree passes
+    kProfSlots
+};
+constexpr int kScProf = 80;  // 16 u64 after the argmax keys (at most 16 warps)
+static_assert(kScProf + 2 * kProfSlots <= kScratchWords, "profile slots exceed the scratch words");
+
 // VC_TRACE builds time the activities of Sec. V-D (thread 0 of each worker, %globaltimer).
+#ifdef VC_TRACE
+#define VC_CYC() clock64()
+#define VC_CYC_ADD(w, slot, t0)                                                      \
+    do {                                                                             \
+        if ((w).tid == 0) (w).prof()[slot] += (unsigned long long)(clock64() - (t0)); \
+    } while (0)
+#define VC_CYC_INC(w, slot)                       \
+    do {                                          \
+        if ((w).tid == 0) (w).prof()[slot] += 1; \
+    } while (0)
+#else
+#define VC_CYC() 0ll
+#define VC_CYC_ADD(w, slot, t0) \
+    do {                        \
+    } while (0)
+#define VC_CYC_INC(w, slot) \
+    do {                    \
+    } while (0)
+#endif
+
 #ifdef VC_TRACE
 #define VC_TRACE_NOW() globaltimer_ns()
 #define VC_TRACE_ADD(w, slot, t0)                                         \
@@ -180,15 +227,51 @@ static_assert(kScTally + 2 * kTallySlots <= 40, "tally overlaps the argmax keys"
     } while (0)
 #endif
 
+// NW-word bit rows as one vector load / store.
+template <int NW> struct RowVec;
+template <> struct RowVec<1> {
+    using type = uint32_t;
+    static __device__ __forceinline__ type pack(const uint32_t (&b)[1]) { return b[0]; }
+    static __device__ __forceinline__ void unpack(type q, uint32_t (&b)[1]) { b[0] = q; }
+};
+template <> struct RowVec<2> {
+    using type = uint2;
+    static __device__ __forceinline__ type pack(const uint32_t (&b)[2]) { return make_uint2(b[0], b[1]); }
+    static __device__ __forceinline__ void unpack(type q, uint32_t (&b)[2]) {
+        b[0] = q.x;
+        b[1] = q.y;
+    }
+};
+template <> struct RowVec<4> {
+    using type = uint4;
+    static __device__ __forceinline__ type pack(const uint32_t (&b)[4]) { return make_uint4(b[0], b[1], b[2], b[3]); }
+    static __device__ __forceinline__ void unpack(type q, uint32_t (&b)[4]) {
+        b[0] = q.x;
+        b[1] = q.y;
+        b[2] = q.z;
+        b[3] = q.w;
+    }
+};
+
 // ------------------------------------------------------------------------------------------------
 // Worker
 // ------------------------------------------------------------------------------------------------
 // GM = false: the node lives in shared memory.  GM = true: the degree array, marks, dirty bits and
 // removal list live in a global-memory region of this worker (the header and scratch stay in
 // shared memory); their reads go through L2 (.cg) because the atomics that change them act there.
-template <typename W, int WT, bool GM = false>
+//
+// NW > 0 (one-warp workers, graphs of at most 32*NW vertices): bit-row worker.  The node is the
+// same degree array, but the rules find neighbours, test adjacency and apply removals through
+// bit rows of the adjacency matrix instead of walking the CSR: a degree-one vertex's neighbour is
+// the lowest bit of row(v) & live; a removal recomputes each live vertex's degree as
+// popc(row(v) & live') lane-parallel, with no atomics.  The rounds, tie-breaks and resulting
+// degree arrays are the same as the CSR walks'.
+template <typename W, int WT, bool GM = false, int NW = 0>
 struct Worker {
+    static_assert(NW == 0 || NW == 1 || NW == 2 || NW == 4, "bit rows of 1, 2 or 4 words");
+    static_assert(NW == 0 || (WT == 32 && !GM), "bit rows are for one-warp shared-memory workers");
     static constexpr int kWarps = WT / 32;
+    static constexpr int kNW = NW > 0 ? NW : 1;  // array extent for the bit-row helpers
     EntryHeader *hdr;
     W *d;
     uint32_t *marks;
@@ -198,6 +281,9 @@ struct Worker {
     unsigned long long *keys;
     unsigned long long *tally;
     int32_t *csr;
+    uint32_t *livew;  // bit-row workers: live-vertex mask (NW words)
+    uint32_t *newm;   // bit-row workers: vertices chosen for S in the current pass (NW words)
+    uint32_t *rows;   // bit-row workers: adjacency bit rows, NW words per vertex
     int tid, lane, warp;
     int32_t entry_bytes;
     int32_t csr_words;
@@ -231,6 +317,9 @@ struct Worker {
         tally = reinterpret_cast<unsigned long long *>(sc + kScTally);
         csr = sc + kScratchWords;
         csr_words = csr_capacity;
+        livew = reinterpret_cast<uint32_t *>(csr) + pad16((int64_t)csr_capacity * 4) / 4;
+        newm = livew + 4;
+        rows = livew + 8;
         staged = -1;
         staged_full = false;
         dbg = nullptr;
@@ -240,6 +329,10 @@ struct Worker {
         lane = tid & 31;
         warp = tid >> 5;
         entry_bytes = eb;
+    }
+
+    __device__ __forceinline__ unsigned long long *prof() const {
+        return reinterpret_cast<unsigned long long *>(sc + kScProf);
     }
 
     // Worker-wide barriers: a one-warp worker needs only a warp barrier (and a warp vote).
@@ -320,24 +413,108 @@ struct Worker {
     }
 
     // Points c at a shared-memory copy of its graph's offsets -- and of its neighbour lists too
-    // when the launch reserved room for them -- copied when the problem changes.
-    __device__ void stage(Ctx &c) {
-        if (csr_words == 0) return;
+    // when the launch reserved room for them -- copied when the problem changes.  Bit-row
+    // workers also load the graph's bit rows: from `grows` (global, written by the greedy pass)
+    // unless `build` is set or grows is null, in which case they are built from the CSR (and
+    // written to grows when it is given).
+    __device__ void stage(Ctx &c, uint32_t *grows = nullptr, bool build = true) {
         const int n1 = c.n + 1;
-        if (n1 > csr_words) return;  // does not fit: keep reading global memory
-        if (c.index != staged) {
+        const bool copy_csr = csr_words > 0 && n1 <= csr_words;
+        if (NW == 0 && !copy_csr) return;  // nothing to stage: read global memory
+        if (c.index == staged) {
+            if (copy_csr) {
+                c.off = csr;
+                if (staged_full) c.adj = csr + n1;
+            }
+            return;
+        }
+        sync();  // nobody still reads the previous copy
+        bool full = false;
+        if (copy_csr) {
             const int len = c.off[c.n];
-            const bool full = n1 + len <= csr_words;
-            sync();  // nobody still reads the previous copy
+            full = n1 + len <= csr_words;
             for (int i = tid; i < n1; i += WT) csr[i] = c.off[i];
             if (full)
                 for (int i = tid; i < len; i += WT) csr[n1 + i] = c.adj[i];
-            staged = c.index;
-            staged_full = full;
-            sync();
         }
-        c.off = csr;
-        if (staged_full) c.adj = csr + n1;
+        if constexpr (NW > 0) stage_rows(c, grows, build);
+        staged = c.index;
+        staged_full = full;
+        sync();
+        if (copy_csr) {
+            c.off = csr;
+            if (full) c.adj = csr + n1;
+        }
+    }
+
+    // Bit rows of the graph (lane-parallel: lane handles vertices lane, lane+32, ...).
+    __device__ void stage_rows(const Ctx &c, uint32_t *grows, bool build) {
+        using V = typename RowVec<kNW>::type;
+        V *r = reinterpret_cast<V *>(rows);
+        if (!build && grows) {
+            const V *g = reinterpret_cast<const V *>(grows);
+            for (int v = lane; v < c.n; v += 32) r[v] = __ldcg(g + v);
+            return;
+        }
+        for (int v = lane; v < c.n; v += 32) {
+            uint32_t b[kNW];
+#pragma unroll
+            for (int w = 0; w < NW; ++w) b[w] = 0u;
+            const int lo = c.off[v], hi = c.off[v + 1];
+            for (int j = lo; j < hi; ++j) {
+                const int x = c.adj[j];
+                VC_CHECK(dbg, x >= 0 && x < 32 * NW, 21, x, continue);
+#pragma unroll
+                for (int w = 0; w < NW; ++w) b[w] |= ((x >> 5) == w) ? (1u << (x & 31)) : 0u;
+            }
+            const V q = RowVec<kNW>::pack(b);
+            r[v] = q;
+            if (grows) __stcg(reinterpret_cast<V *>(grows) + v, q);
+        }
+    }
+
+    // ---- bit-row helpers (NW > 0) --------------------------------------------------------------
+
+    __device__ __forceinline__ void row(int v, uint32_t (&b)[kNW]) const {
+        RowVec<kNW>::unpack(reinterpret_cast<const typename RowVec<kNW>::type *>(rows)[v], b);
+    }
+    __device__ __forceinline__ void live_words(uint32_t (&b)[kNW]) const {
+#pragma unroll
+        for (int w = 0; w < NW; ++w) b[w] = livew[w];
+    }
+    // Lowest set bit over NW words, or -1.
+    static __device__ __forceinline__ int first_bit(const uint32_t (&b)[kNW]) {
+        int u = -1;
+#pragma unroll
+        for (int w = NW - 1; w >= 0; --w)
+            if (b[w]) u = 32 * w + __ffs(b[w]) - 1;
+        return u;
+    }
+    // Clears the lowest set bit over NW words.
+    static __device__ __forceinline__ void clear_first(uint32_t (&b)[kNW]) {
+        bool done = false;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            if (!done && b[w]) {
+                b[w] &= b[w] - 1u;
+                done = true;
+            }
+        }
+    }
+    __device__ __forceinline__ bool row_has(int u, int x) const { return (rows[u * NW + (x >> 5)] >> (x & 31)) & 1u; }
+
+    // Live mask of the current node from its degree array (after a node is loaded).
+    __device__ void init_live(const Ctx &c) {
+#pragma unroll
+        for (int k = 0; k < NW; ++k) {
+            const int v = 32 * k + lane;
+            const unsigned m = __ballot_sync(kFull, v < c.n && deg(v) != -1);
+            if (lane == 0) {
+                livew[k] = m;
+                newm[k] = 0u;
+            }
+        }
+        __syncwarp();
     }
 
     // ---- node loading / storing ---------------------------------------------------------------
@@ -355,6 +532,7 @@ struct Worker {
             hdr->branch = -1;
         }
         sync();
+        if constexpr (NW > 0) init_live(c);
     }
 
     // Copies an entry of `bytes` (header + degree array of the entry's graph) from global memory.
@@ -439,12 +617,206 @@ struct Worker {
         sync();
     }
 
-    // Ends a pass: returns true (and applies the removal) iff some thread proposed a vertex.
-    __device__ __forceinline__ bool finish_pass(const Ctx &c, bool proposed) {
+    // ---- bit-row removal and rules (NW > 0) -------------------------------------------------------
+
+    // Moves the chosen set newm into S: every live vertex outside it gets its degree recomputed as
+    // popc(row & live'), a vertex whose degree changed is marked dirty for both passes, and
+    // m = (sum of live degrees) / 2.  Same result as apply_list's decrements.
+    __device__ void apply_rows(const Ctx &c) {
+        __syncwarp();  // every proposal (shared atomics) is done
+        uint32_t rm[kNW], nl[kNW];
+        int cnt = 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            rm[w] = newm[w];
+            nl[w] = livew[w] & ~rm[w];
+            cnt += __popc(rm[w]);
+        }
+        int degsum = 0, words = 0;
+#pragma unroll
+        for (int k = 0; k < NW; ++k) {
+            const int v = 32 * k + lane;
+            bool changed = false;
+            if (v < c.n) {
+                const int dv = deg(v);
+                if ((rm[k] >> lane) & 1u) {
+                    d[v] = (W)-1;
+                    words += c.off[v + 1] - c.off[v];
+                } else if (dv >= 0) {
+                    uint32_t b[kNW];
+                    row(v, b);
+                    int nd = 0;
+#pragma unroll
+                    for (int w = 0; w < NW; ++w) nd += __popc(b[w] & nl[w]);
+                    if (nd != dv) {
+                        d[v] = (W)nd;
+                        changed = true;
+                    }
+                    degsum += nd;
+                }
+            }
+            const unsigned chg = __ballot_sync(kFull, changed);
+            if (lane == 0 && chg) dirty[k] |= (unsigned long long)chg * 0x100000001ull;
+        }
+        degsum = __reduce_add_sync(kFull, degsum);
+        words = __reduce_add_sync(kFull, words);
+        if (lane == 0) {
+            hdr->S += cnt;
+            hdr->m = degsum / 2;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) {
+                livew[w] = nl[w];
+                newm[w] = 0u;
+            }
+            tally[kTCsr] += (unsigned long long)words;
+        }
+        __syncwarp();
+    }
+
+    // Ends a bit-row scan: returns whether any lane chose a vertex (the choice waits in newm).
+    __device__ __forceinline__ bool rows_finish(bool proposed, int words, int slot, long long t0) {
+        words = __reduce_add_sync(kFull, words);
+        if (lane == 0) {
+            tally[kTPasses] += 1;
+            tally[kTCsr] += (unsigned long long)words;
+        }
+        const bool any = __any_sync(kFull, proposed);
+        VC_CYC_ADD(*this, slot, t0);
+        VC_CYC_INC(*this, slot + (kPDeg1Count - kPDeg1));
+        return any;
+    }
+
+    // Degree-one over bit rows: a dirty degree-one vertex's neighbour is the lowest bit of
+    // row(v) & live (one lane per vertex; same tie-break as pass_degree_one).
+    __device__ bool rows_pass_degree_one(const Ctx &c) {
+        const long long t0 = VC_CYC();
+        uint32_t lv[kNW];
+        live_words(lv);
+        bool proposed = false;
+        int words = 0;
+#pragma unroll
+        for (int k = 0; k < NW; ++k) {
+            if (32 * k >= c.n) break;
+            const unsigned long long dw = dirty[k];
+            const unsigned bits = (unsigned)dw;
+            if (bits == 0u) continue;
+            if (lane == 0) dirty[k] = dw & 0xffffffff00000000ull;
+            const int v = 32 * k + lane;
+            if (((bits >> lane) & 1u) && v < c.n && deg(v) == 1) {
+                uint32_t b[kNW];
+                row(v, b);
+#pragma unroll
+                for (int w = 0; w < NW; ++w) b[w] &= lv[w];
+                const int u = first_bit(b);
+                words += c.off[v + 1] - c.off[v];
+                if (u >= 0 && !(deg(u) == 1 && u > v)) {
+                    atomicOr(&newm[u >> 5], 1u << (u & 31));
+                    proposed = true;
+                }
+            }
+        }
+        return rows_finish(proposed, words, kPDeg1, t0);
+    }
+
+    // Degree-two-triangle over bit rows: the two lowest bits of row(v) & live are u < w, and uw is
+    // an edge iff bit w of row(u) is set (same tie-break as pass_degree_two_triangle).
+    __device__ bool rows_pass_degree_two_triangle(const Ctx &c) {
+        const long long t0 = VC_CYC();
+        uint32_t lv[kNW];
+        live_words(lv);
+        bool proposed = false;
+        int words = 0;
+#pragma unroll
+        for (int k = 0; k < NW; ++k) {
+            if (32 * k >= c.n) break;
+            const unsigned long long dw = dirty[k];
+            const unsigned bits = (unsigned)(dw >> 32);
+            if (bits == 0u) continue;
+            if (lane == 0) dirty[k] = dw & 0xffffffffull;
+            const int v = 32 * k + lane;
+            if (((bits >> lane) & 1u) && v < c.n && deg(v) == 2) {
+                uint32_t b[kNW];
+                row(v, b);
+#pragma unroll
+                for (int w = 0; w < NW; ++w) b[w] &= lv[w];
+                const int u = first_bit(b);
+                clear_first(b);
+                const int x = first_bit(b);
+                words += c.off[v + 1] - c.off[v];
+                if (u >= 0 && x >= 0) {
+                    words += min(c.off[u + 1] - c.off[u], c.off[x + 1] - c.off[x]);
+                    if (row_has(u, x) && !((deg(u) == 2 && u < v) || (deg(x) == 2 && x < v))) {
+                        atomicOr(&newm[u >> 5], 1u << (u & 31));
+                        atomicOr(&newm[x >> 5], 1u << (x & 31));
+                        proposed = true;
+                    }
+                }
+            }
+        }
+        return rows_finish(proposed, words, kPTri, t0);
+    }
+
+    // High-degree over the lanes' own vertices: one ballot per 32 vertices.
+    __device__ bool rows_pass_high_degree(const Ctx &c, int32_t bound) {
+        const long long t0 = VC_CYC();
+        const int thr = (c.kind == kMVC) ? bound - hdr->S - 1 : bound - hdr->S;
+        bool proposed = false;
+#pragma unroll
+        for (int k = 0; k < NW; ++k) {
+            if (32 * k >= c.n) break;
+            const int v = 32 * k + lane;
+            const int dv = v < c.n ? deg(v) : -1;
+            const unsigned m = __ballot_sync(kFull, dv != -1 && dv > thr);
+            if (lane == 0) newm[k] = m;
+            proposed |= m != 0u;
+        }
+        return rows_finish(proposed, 0, kPHigh, t0);
+    }
+
+    // Ends a scan: returns whether some thread proposed a vertex (the proposals wait in the
+    // removal list).  (slot, t0: VC_TRACE accounting of the scan.)
+    __device__ __forceinline__ bool finish_pass(bool proposed, int slot, long long t0) {
         if (tid == 0) tally[kTPasses] += 1;
-        if (!sync_or(proposed)) return false;
-        apply_list(c);
-        return true;
+        const bool any = sync_or(proposed);
+        VC_CYC_ADD(*this, slot, t0);
+        VC_CYC_INC(*this, slot + (kPDeg1Count - kPDeg1));
+        return any;
+    }
+
+    // Whether a branch left a removal waiting (uniform; take_vertex / take_neighbourhood end with
+    // a barrier).
+    __device__ __forceinline__ bool has_pending() const {
+        if constexpr (NW > 0) {
+            bool any = false;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) any |= newm[w] != 0u;
+            return any;
+        } else {
+            return sc[kScCount] != 0;
+        }
+    }
+
+    // Drops a pending removal (a node abandoned before its reduction).
+    __device__ void discard_pending() {
+        if constexpr (NW > 0) {
+            if (lane == 0) {
+#pragma unroll
+                for (int w = 0; w < NW; ++w) newm[w] = 0u;
+            }
+        } else {
+            const int cnt = sc[kScCount];
+            for (int i = tid; i < cnt; i += WT) marks[ld_list(i) >> 5] = 0u;
+            sync();
+            if (tid == 0) sc[kScCount] = 0;
+        }
+        sync();
+    }
+
+    __device__ __forceinline__ void apply(const Ctx &c) {
+        const long long t1 = VC_CYC();
+        if constexpr (NW > 0) apply_rows(c);
+        else apply_list(c);
+        VC_CYC_ADD(*this, kPApply, t1);
     }
 
     // ---- warp-cooperative adjacency scans --------------------------------------------------------
@@ -508,6 +880,8 @@ struct Worker {
     // Degree-one: the live neighbour u of a degree-one vertex v enters S; if u also has degree one
     // (an isolated edge) only the smaller id of the pair enters.
     __device__ bool pass_degree_one(const Ctx &c) {
+        if constexpr (NW > 0) return rows_pass_degree_one(c);
+        const long long t0 = VC_CYC();
         bool proposed = false;
         int words = 0;
         for (int base = warp * 32; base < c.n; base += WT) {
@@ -531,12 +905,14 @@ struct Worker {
             }
         }
         if (lane == 0 && words) atomicAdd(&tally[kTCsr], (unsigned long long)words);
-        return finish_pass(c, proposed);
+        return finish_pass(proposed, kPDeg1, t0);
     }
 
     // Degree-two-triangle: if N(v) = {u, w} and uw is an edge, u and w enter S; among degree-two
     // vertices of one triangle only the smallest id applies the rule.
     __device__ bool pass_degree_two_triangle(const Ctx &c) {
+        if constexpr (NW > 0) return rows_pass_degree_two_triangle(c);
+        const long long t0 = VC_CYC();
         bool proposed = false;
         int words = 0;
         for (int base = warp * 32; base < c.n; base += WT) {
@@ -562,7 +938,7 @@ struct Worker {
             }
         }
         if (lane == 0 && words) atomicAdd(&tally[kTCsr], (unsigned long long)words);
-        return finish_pass(c, proposed);
+        return finish_pass(proposed, kPTri, t0);
     }
 
     // High-degree: a vertex whose degree exceeds the threshold enters S.  Threshold best-|S|-1
@@ -570,6 +946,8 @@ struct Worker {
     // spare argmax() its own scan after the last pass, measured 5 % slower: every pass paid for
     // keys only the last one needs.)
     __device__ bool pass_high_degree(const Ctx &c, int32_t bound) {
+        if constexpr (NW > 0) return rows_pass_high_degree(c, bound);
+        const long long t0 = VC_CYC();
         const int thr = (c.kind == kMVC) ? bound - hdr->S - 1 : bound - hdr->S;
         bool proposed = false;
         for (int v = tid; v < c.n; v += WT) {
@@ -579,7 +957,7 @@ struct Worker {
                 proposed = true;
             }
         }
-        return finish_pass(c, proposed);
+        return finish_pass(proposed, kPHigh, t0);
     }
 
     // |S| part of the stop check: MVC needs |S| < best, PVC needs |S| <= k.
@@ -587,30 +965,37 @@ struct Worker {
         return (c.kind == kMVC) ? hdr->S >= bound : hdr->S > bound;
     }
 
-    // Applies the chosen rules until a whole round changes nothing.  With early_exit, returns true
-    // as soon as |S| alone prunes the node (sound: |S| only grows); otherwise runs to the fixpoint.
+    // Applies a pending branch removal, then the chosen rules in the order degree-one,
+    // degree-two-triangle, high-degree, cyclically, until every chosen rule in a row has found
+    // nothing.  This is the fixpoint of repeating whole rounds until a round changes nothing: a
+    // rule that found nothing in a state finds nothing in it again, so the passes a round-based
+    // loop would add after that point cannot change the state.  With early_exit, returns true as
+    // soon as |S| alone prunes the node (sound: |S| only grows).  The removal is applied at this
+    // one place, which keeps the kernel's code small.
     __device__ bool reduce(const Ctx &c, int32_t bound, int rules, bool early_exit) {
+        const int nrules = __popc(rules & kRuleAll);
+        int quiet = 0, r = 0;
+        bool pend = has_pending();
+        if (early_exit && size_exceeded(c, bound)) {  // best fell since the node was made
+            if (pend) discard_pending();
+            return true;
+        }
         for (;;) {
-            bool changed = false;
-            if (rules & kRuleDeg1) {
-                if (pass_degree_one(c)) {
-                    changed = true;
-                    if (early_exit && size_exceeded(c, bound)) return true;
-                }
+            if (pend) {
+                apply(c);
+                quiet = 0;
+                if (early_exit && size_exceeded(c, bound)) return true;
             }
-            if (rules & kRuleDeg2Tri) {
-                if (pass_degree_two_triangle(c)) {
-                    changed = true;
-                    if (early_exit && size_exceeded(c, bound)) return true;
-                }
+            if (quiet >= nrules) return false;
+            const bool on = (rules >> r) & 1;
+            pend = false;
+            if (on) {
+                if (r == 0) pend = pass_degree_one(c);
+                else if (r == 1) pend = pass_degree_two_triangle(c);
+                else pend = pass_high_degree(c, bound);
+                if (!pend) ++quiet;
             }
-            if (rules & kRuleHigh) {
-                if (pass_high_degree(c, bound)) {
-                    changed = true;
-                    if (early_exit && size_exceeded(c, bound)) return true;
-                }
-            }
-            if (!changed) return false;
+            r = (r == 2) ? 0 : r + 1;
         }
     }
 
@@ -643,28 +1028,44 @@ struct Worker {
         return key == 0ull ? -1 : (int)(0xffffffffu - (uint32_t)key);
     }
 
-    // Puts the single vertex v into S (the "v" child of Sec. II-B).
+    // Puts the single vertex v into S (the "v" child of Sec. II-B).  The removal is left pending
+    // and applied by the next reduce().
     __device__ void take_vertex(const Ctx &c, int v) {
         VC_CHECK(dbg, v >= 0 && v < c.n, 5, v, return);
+        if constexpr (NW > 0) {
+            if (lane == 0) newm[v >> 5] = 1u << (v & 31);  // newm is empty between passes
+            __syncwarp();
+            return;
+        }
         if (tid == 0) propose(v);
         sync();
-        apply_list(c);
     }
 
-    // Puts every live neighbour of v into S (the "N(v)" child of Sec. II-B).
+    // Puts every live neighbour of v into S (the "N(v)" child of Sec. II-B).  The removal is left
+    // pending and applied by the next reduce().
     __device__ void take_neighbourhood(const Ctx &c, int v) {
         VC_CHECK(dbg, v >= 0 && v < c.n, 6, v, return);
+        if constexpr (NW > 0) {
+            uint32_t b[kNW], lv[kNW];
+            row(v, b);
+            live_words(lv);
+#pragma unroll
+            for (int w = 0; w < NW; ++w) b[w] &= lv[w];
+            if (lane == 0) {
+#pragma unroll
+                for (int w = 0; w < NW; ++w) newm[w] = b[w];
+                tally[kTCsr] += (unsigned long long)(c.off[v + 1] - c.off[v]);
+            }
+            __syncwarp();
+            return;
+        }
         const int lo = c.off[v], hi = c.off[v + 1];
-        bool proposed = false;
         for (int j = lo + tid; j < hi; j += WT) {
             const int x = c.adj[j];
-            if (deg(x) != -1) {
-                propose(x);
-                proposed = true;
-            }
+            if (deg(x) != -1) propose(x);
         }
         if (tid == 0) atomicAdd(&tally[kTCsr], (unsigned long long)(hi - lo));
-        if (sync_or(proposed)) apply_list(c);
+        sync();
     }
 
     // Writes the current node's S as a 0/1 mask.

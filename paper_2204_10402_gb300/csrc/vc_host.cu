@@ -33,7 +33,7 @@ struct Workspace {
     int device = -1;
     int sms = 0;
     int smem_optin = 0;
-    DevBuf csr_off, csr_adj, problems, adj_len, ctrl, cover, stacks, wl_slots, wl_seq, sm_nodes, gstate;
+    DevBuf csr_off, csr_adj, problems, adj_len, ctrl, cover, stacks, wl_slots, wl_seq, sm_nodes, gstate, rows;
     void *pinned = nullptr;
     size_t pinned_cap = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -113,7 +113,7 @@ int workspace(Workspace **out) {
 
 void free_workspace(Workspace &ws) {
     DevBuf *bufs[] = {&ws.csr_off, &ws.csr_adj, &ws.problems, &ws.adj_len, &ws.ctrl, &ws.cover,
-                      &ws.stacks, &ws.wl_slots, &ws.wl_seq, &ws.sm_nodes, &ws.gstate};
+                      &ws.stacks, &ws.wl_slots, &ws.wl_seq, &ws.sm_nodes, &ws.gstate, &ws.rows};
     for (DevBuf *b : bufs) {
         if (b->p) cudaFree(b->p);
         b->p = nullptr;
@@ -149,7 +149,7 @@ struct Result {
     std::vector<Problem> probs;
     Control ctrl;
     float kernel_ms = 0.f;
-    int workers = 0, wt = 0, width = 0, stack_depth = 0;
+    int workers = 0, wt = 0, width = 0, stack_depth = 0, nw = 0;
     bool csr_staged = false, gm = false;
 };
 
@@ -213,7 +213,13 @@ int run(Workspace &ws, const Spec &spec, const vc_config *cfg_in, cudaStream_t s
         smem = smem_bytes_gm(csr_words);
     }
     if (smem > ws.smem_optin) return VC_EINVAL;  // graph too large for a shared-memory degree array
-    const Launchers &L = launchers(width, gm);
+    // Bit-row workers: one warp per worker, node in shared memory, n_max <= 128.
+    int nw = 0;
+    if (cfg.bit_rows >= 0 && !gm && wt == 32) nw = rows_words_for(n_max);
+    if (cfg.bit_rows > 0 && nw == 0) return VC_EINVAL;
+    if (nw > 0 && smem + rows_bytes_for(n_max, nw) <= ws.smem_optin) smem += rows_bytes_for(n_max, nw);
+    else nw = 0;
+    const Launchers &L = launchers(width, gm, nw);
     int per_sm = 0;
     VC_RC(L.occupancy(wt, smem, &per_sm));
     if (per_sm <= 0) return VC_EINVAL;
@@ -288,6 +294,10 @@ int run(Workspace &ws, const Spec &spec, const vc_config *cfg_in, cudaStream_t s
         VC_RC(grow(ws.gstate, (size_t)workers * (size_t)P.gstate_bytes));
         P.gstate = static_cast<uint8_t *>(ws.gstate.p);
     }
+    if (nw > 0) {  // the greedy pass writes each graph's bit rows here; the traversal copies them
+        VC_RC(grow(ws.rows, sizeof(uint32_t) * (size_t)nw * (size_t)std::max<int64_t>(spec.total_vertices, 1)));
+        P.rows = static_cast<uint32_t *>(ws.rows.p);
+    }
 
     if (!cfg.skip_validation)
         VC_RC(launch_validate(d_off, d_adj, d_probs, static_cast<const int64_t *>(ws.adj_len.p), G,
@@ -354,6 +364,7 @@ int run(Workspace &ws, const Spec &spec, const vc_config *cfg_in, cudaStream_t s
     res.width = width;
     res.csr_staged = csr_words > 0;
     res.gm = gm;
+    res.nw = nw;
     res.stack_depth = spec.search ? (int)depth : 0;
     return h_ctrl->status;
 }
@@ -371,6 +382,7 @@ void fill_stats(vc_stats *st, const Result &r, double total_ms, int32_t greedy) 
     st->entry_bytes_moved = (int64_t)r.ctrl.entry_bytes;
     for (int i = 0; i < 4; ++i) st->trace_ns[i] = (int64_t)r.ctrl.trace_ns[i];
     st->idle_polls = (int64_t)r.ctrl.idle_polls;
+    for (int i = 0; i < 16; ++i) st->trace_cycles[i] = (int64_t)r.ctrl.trace_cycles[i];
     st->max_depth = r.ctrl.max_depth;
     st->greedy_ub = greedy;
     st->workers = r.workers;
@@ -378,6 +390,7 @@ void fill_stats(vc_stats *st, const Result &r, double total_ms, int32_t greedy) 
     st->width = r.width;
     st->csr_staged = r.csr_staged ? 1 : 0;
     st->node_in_global = r.gm ? 1 : 0;
+    st->bit_rows = r.nw;
     st->stack_depth = r.stack_depth;
     st->status = r.ctrl.status;
     st->kernel_ms = r.kernel_ms;
@@ -570,6 +583,9 @@ int vc_reduce_node(const vc_graph *g, int32_t *deg, int32_t *S, int32_t *m, int3
     const bool gm = c.node_in_global > 0 || (c.node_in_global == 0 && smem > ws->smem_optin);
     if (gm) smem = smem_bytes_gm(0);
     if (smem > ws->smem_optin) return VC_EINVAL;
+    int nw = (c.bit_rows >= 0 && !gm && wt == 32) ? rows_words_for(g->n) : 0;
+    if (c.bit_rows > 0 && nw == 0) return VC_EINVAL;
+    smem += rows_bytes_for(g->n, nw);
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t len = g->on_device ? -1 : g->offsets[g->n];
     // device copies: graph (if host), degree array, io words
@@ -626,7 +642,7 @@ int vc_reduce_node(const vc_graph *g, int32_t *deg, int32_t *S, int32_t *m, int3
         VC_RC(grow(ws->gstate, (size_t)gstate_bytes_for(g->n, width / 8)));
         R.gstate = static_cast<uint8_t *>(ws->gstate.p);
     }
-    const Launchers &L = launchers(width, gm);
+    const Launchers &L = launchers(width, gm, nw);
     VC_RC(L.reduce(wt, smem, s, R));
     VC_CK(cudaMemcpyAsync(deg, d_deg, deg_bytes, g->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
     VC_CK(cudaMemcpyAsync(h_io, d_io, 3 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));

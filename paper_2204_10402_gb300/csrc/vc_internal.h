@@ -82,6 +82,7 @@ struct alignas(128) Control {
     unsigned long long entry_bytes;
     unsigned long long trace_ns[4];  // VC_TRACE builds: ns waiting for work, reducing, branching, solutions
     unsigned long long idle_polls;   // VC_TRACE builds: idle-loop iterations
+    unsigned long long trace_cycles[16];  // VC_TRACE builds: SM cycles per activity (ProfSlot)
 };
 
 // Kernel arguments (passed by value).
@@ -103,6 +104,8 @@ struct Params {
     int32_t csr_words;       // shared-memory CSR staging capacity in int32 words (0 = read the CSR from global)
     uint8_t *gstate;         // global-memory node state, gstate_bytes per worker (global-state kernels)
     int32_t gstate_bytes;
+    uint32_t *rows;          // bit-row kernels: NW words per vertex, at cover_base * NW per problem
+                             // (written by the greedy pass); null = each worker builds its own
     int64_t idle_timeout_ns;
     const volatile int32_t *cancel;
     unsigned long long *sm_nodes;  // per-SM node counters
@@ -193,6 +196,12 @@ VC_HD inline int32_t default_worklist_capacity(int32_t entry_bytes) {
 VC_HD inline int32_t smem_bytes_gm(int32_t csr_words) {
     return 16 + kScratchWords * 4 + pad16((int64_t)csr_words * 4);
 }
+// Bit-row workers (NW = 1, 2 or 4 words per row, graphs of at most 32 * NW vertices): the live
+// mask and chosen set (16 B each) and n_max rows after the staged CSR.
+VC_HD inline int32_t rows_bytes_for(int32_t n_max, int32_t nw) {
+    return nw > 0 ? 32 + pad16((int64_t)n_max * nw * 4) : 0;
+}
+VC_HD inline int32_t rows_words_for(int32_t n_max) { return n_max <= 32 ? 1 : n_max <= 64 ? 2 : n_max <= 128 ? 4 : 0; }
 VC_HD inline int32_t gstate_bytes_for(int32_t n_max, int32_t width_bytes) {
     int64_t b = pad16((int64_t)n_max * width_bytes);
     b += pad16(((int64_t)n_max + 31) / 32 * 4);

@@ -2,9 +2,5 @@
 #include "vc_launch_impl.cuh"
 
 namespace vc {
-const Launchers &launchers_w16() {
-    using I = LaunchImpl<int16_t, false>;
-    static const Launchers L = {&I::greedy, &I::traverse, &I::reduce, &I::occupancy};
-    return L;
-}
+const Launchers &launchers_w16() { return LaunchImpl<int16_t, false, 0>::table(); }
 }  // namespace vc

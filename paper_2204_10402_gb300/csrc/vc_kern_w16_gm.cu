@@ -3,9 +3,5 @@
 #include "vc_launch_impl.cuh"
 
 namespace vc {
-const Launchers &launchers_w16_gm() {
-    using I = LaunchImpl<int16_t, true>;
-    static const Launchers L = {&I::greedy, &I::traverse, &I::reduce, &I::occupancy};
-    return L;
-}
+const Launchers &launchers_w16_gm() { return LaunchImpl<int16_t, true, 0>::table(); }
 }  // namespace vc

@@ -2,9 +2,5 @@
 #include "vc_launch_impl.cuh"
 
 namespace vc {
-const Launchers &launchers_w32() {
-    using I = LaunchImpl<int32_t, false>;
-    static const Launchers L = {&I::greedy, &I::traverse, &I::reduce, &I::occupancy};
-    return L;
-}
+const Launchers &launchers_w32() { return LaunchImpl<int32_t, false, 0>::table(); }
 }  // namespace vc

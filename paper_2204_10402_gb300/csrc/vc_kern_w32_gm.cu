@@ -3,9 +3,5 @@
 #include "vc_launch_impl.cuh"
 
 namespace vc {
-const Launchers &launchers_w32_gm() {
-    using I = LaunchImpl<int32_t, true>;
-    static const Launchers L = {&I::greedy, &I::traverse, &I::reduce, &I::occupancy};
-    return L;
-}
+const Launchers &launchers_w32_gm() { return LaunchImpl<int32_t, true, 0>::table(); }
 }  // namespace vc

@@ -33,8 +33,15 @@ __global__ void init_worklist_kernel(uint32_t *seq, int32_t capacity, Control *c
 // PVC found flag when the greedy cover already fits) in its record.  Returns whether a search is
 // still needed (uniform across the block).
 // ------------------------------------------------------------------------------------------------
-template <typename W, int WT, bool GM>
-__device__ bool greedy_solve(const Params &P, Worker<W, WT, GM> &w, Ctx &c) {
+// Where a problem's bit rows live in global memory (bit-row kernels), or null.
+template <int NW>
+__device__ __forceinline__ uint32_t *rows_of(const Params &P, const Ctx &c) {
+    if constexpr (NW == 0) return nullptr;
+    else return P.rows ? P.rows + (size_t)(c.cover - P.cover) * NW : nullptr;
+}
+
+template <typename W, int WT, bool GM, int NW>
+__device__ bool greedy_solve(const Params &P, Worker<W, WT, GM, NW> &w, Ctx &c) {
     w.cur_n = c.n;
     if (c.n == 0) {
         w.sync();
@@ -46,7 +53,7 @@ __device__ bool greedy_solve(const Params &P, Worker<W, WT, GM> &w, Ctx &c) {
         w.sync();
         return false;
     }
-    w.stage(c);
+    w.stage(c, rows_of<NW>(P, c), true);
     w.load_root(c);
     const int32_t m0 = w.hdr->m;
     for (;;) {
@@ -73,10 +80,10 @@ __device__ bool greedy_solve(const Params &P, Worker<W, WT, GM> &w, Ctx &c) {
     return c.kind == kMVC ? S > 0 : (c.k >= 0 && S > c.k);
 }
 
-template <typename W, int WT, bool GM>
+template <typename W, int WT, bool GM, int NW>
 __global__ void __launch_bounds__(WT) greedy_kernel(Params P) {
     extern __shared__ __align__(16) uint8_t smem[];
-    Worker<W, WT, GM> w(smem, P.n_max, P.csr_words, P.gstate + (size_t)blockIdx.x * (size_t)P.gstate_bytes);
+    Worker<W, WT, GM, NW> w(smem, P.n_max, P.csr_words, P.gstate + (size_t)blockIdx.x * (size_t)P.gstate_bytes);
     w.init_scratch(P.n_max);
     if (w.tid == 0) w.sc[kScB0] = ld_relaxed(&P.ctrl->status);
     w.sync();
@@ -184,8 +191,8 @@ __device__ __forceinline__ bool cover_lock(const Params &P, Problem *pr) {
 // An edgeless node passed the stop check: MVC lowers best (atomicMin) and, if it still holds the
 // smallest size under the cover lock, writes its cover; PVC raises the found flag and the first
 // worker to raise it writes the cover (Sec. IV-A).
-template <typename W, int WT, bool GM>
-__device__ void record_solution(const Params &P, Worker<W, WT, GM> &w, const Ctx &c) {
+template <typename W, int WT, bool GM, int NW>
+__device__ void record_solution(const Params &P, Worker<W, WT, GM, NW> &w, const Ctx &c) {
     const int32_t S = w.hdr->S;
     bool locked = false, write = false;
     if (w.tid == 0) {
@@ -278,8 +285,8 @@ __device__ __forceinline__ int serve_wait(const Params &P, int &arg) {
 // worklist; idles with a growing sleep while other workers still hold work.  Returns 0 (stop),
 // 1 (a root is loaded) or 2 (a worklist entry is loaded).  Sec. IV-C: the search is over when
 // the worklist is empty and no worker holds work, i.e. when no work unit is left.
-template <typename W, int WT, bool GM>
-__device__ int acquire(const Params &P, Worker<W, WT, GM> &w) {
+template <bool SERVE, typename W, int WT, bool GM, int NW>
+__device__ int acquire(const Params &P, Worker<W, WT, GM, NW> &w) {
     Control *ctrl = P.ctrl;
     if (w.tid == 0) {
         int result = 0, arg = 0;
@@ -292,7 +299,7 @@ __device__ int acquire(const Params &P, Worker<W, WT, GM> &w) {
                 break;
             }
         }
-        if (!result && P.serving) {
+        if (SERVE && !result && P.serving) {
             result = serve_wait(P, arg);
         } else if (!result) {
             // The wait ends with work, with the end of the search, or after idle_timeout_ns during
@@ -362,10 +369,12 @@ __device__ int acquire(const Params &P, Worker<W, WT, GM> &w) {
 // ------------------------------------------------------------------------------------------------
 // At most 64 registers per thread, so every worker size keeps 2048 threads resident per SM
 // (measured: the uncapped build used 72 registers, fit 28 one-warp blocks per SM and ran 4 % slower).
-template <typename W, int WT, bool GM>
+// SERVE: the launch also takes requests from a server's ring (the instance the server launches);
+// batch launches use the instance without that path, which keeps their code smaller.
+template <typename W, int WT, bool GM, int NW, bool SERVE>
 __global__ void __launch_bounds__(WT, 1024 / WT) traverse_kernel(Params P) {
     extern __shared__ __align__(16) uint8_t smem[];
-    Worker<W, WT, GM> w(smem, P.n_max, P.csr_words, P.gstate + (size_t)blockIdx.x * (size_t)P.gstate_bytes);
+    Worker<W, WT, GM, NW> w(smem, P.n_max, P.csr_words, P.gstate + (size_t)blockIdx.x * (size_t)P.gstate_bytes);
     w.init_scratch(P.n_max);
     Control *ctrl = P.ctrl;
     w.dbg = ctrl;
@@ -388,42 +397,53 @@ __global__ void __launch_bounds__(WT, 1024 / WT) traverse_kernel(Params P) {
         w.sync();
         // ---- acquire: local stack first (Sec. IV-A), then a root or the worklist ----
         if (top > 0) {
+            const long long t_pop = VC_CYC();
             --top;
             w.load_entry(stack + (size_t)top * eb, eb, P.n_max);
+            if constexpr (NW > 0) w.init_live(c);
             if (w.tid == 0) {
                 w.tally[kTPops] += 1;
                 w.tally[kTBytes] += (unsigned long long)eb;
             }
+            VC_CYC_ADD(w, kPPop, t_pop);
         } else {
             if (cur >= 0 && w.tid == 0) release_unit(P, cur);
             cur = -1;
             const unsigned long long t_wait = VC_TRACE_NOW();
-            int got = acquire(P, w);
+            const long long t_acq = VC_CYC();
+            int got = acquire<SERVE>(P, w);
             VC_TRACE_ADD(w, kTWaitNs, t_wait);
+            VC_CYC_ADD(w, kPAcquire, t_acq);
             if (got == 0) break;
-            if (got == 3) {  // serving: a new request; this worker holds its unit
-                cur = w.sc[kScB5];
-                c = make_ctx(P, cur);
-                VC_CHECK(ctrl, c.n >= 0 && c.n <= P.n_max, 19, c.n, { stop = true; break; });
-                if (!greedy_solve(P, w, c)) continue;  // answered by the greedy bound: release
-                w.load_root(c);
+            if (SERVE && got == 3) {  // serving: a new request; this worker holds its unit
+                if constexpr (SERVE) {
+                    cur = w.sc[kScB5];
+                    c = make_ctx(P, cur);
+                    VC_CHECK(ctrl, c.n >= 0 && c.n <= P.n_max, 19, c.n, { stop = true; break; });
+                    if (!greedy_solve(P, w, c)) continue;  // answered by the greedy bound: release
+                    w.load_root(c);
+                }
             } else {
                 cur = w.hdr->problem;
                 VC_CHECK(ctrl, cur >= 0 && cur < P.num_problems, 1, cur, { stop = true; break; });
                 c = make_ctx(P, cur);
                 VC_CHECK(ctrl, c.n >= 0 && c.n <= P.n_max, 14, c.n, { stop = true; break; });
                 w.cur_n = c.n;
-                w.stage(c);
+                w.stage(c, rows_of<NW>(P, c), false);
+                if constexpr (NW > 0) w.init_live(c);
             }
         }
         VC_CHECK(ctrl, w.hdr->branch < c.n, 13, w.hdr->branch, { stop = true; break; });
         if (w.hdr->branch >= 0) {  // a lazily stored N(v) child: apply the removal now
+            const long long t_tn = VC_CYC();
             w.take_neighbourhood(c, w.hdr->branch);
             if (w.tid == 0) w.hdr->branch = -1;
+            VC_CYC_ADD(w, kPTakeN, t_tn);
         }
 
         // ---- expand nodes, continuing into the "v" child after each branch ----
         for (;;) {
+            const long long t_hdr = VC_CYC();
             if (w.tid == 0) {
                 if ((++w.tally[kTNodes] & 31) == 0) atomicAdd(&ctrl->heartbeat, 1u);
                 w.sc[kScB0] = (c.kind == kMVC) ? ld_relaxed(&c.prob->best) : c.k;
@@ -432,27 +452,36 @@ __global__ void __launch_bounds__(WT, 1024 / WT) traverse_kernel(Params P) {
             }
             w.sync();
             const int32_t bound = w.sc[kScB0];  // one snapshot of best per node (reading R3)
+            VC_CYC_ADD(w, kPHeader, t_hdr);
             if (w.sc[kScB2] != VC_OK) {
                 stop = true;
                 break;
             }
             if (w.sc[kScB1]) {  // PVC already answered: drop this problem's remaining work
+                w.discard_pending();
                 top = 0;
                 break;
             }
-            if (w.size_exceeded(c, bound)) break;
             const unsigned long long t_red = VC_TRACE_NOW();
-            const bool pruned = w.reduce(c, bound, kRuleAll, true) || w.must_stop(c, bound);
+            const bool reduced_out = w.reduce(c, bound, kRuleAll, true);
+            const long long t_stop = VC_CYC();
+            const bool pruned = reduced_out || w.must_stop(c, bound);
+            VC_CYC_ADD(w, kPStop, t_stop);
             VC_TRACE_ADD(w, kTReduceNs, t_red);
             if (pruned) break;
             if (w.hdr->m == 0) {
                 const unsigned long long t_sol = VC_TRACE_NOW();
+                const long long t_solc = VC_CYC();
                 record_solution(P, w, c);
                 VC_TRACE_ADD(w, kTSolutionNs, t_sol);
+                VC_CYC_ADD(w, kPSolution, t_solc);
                 break;
             }
             const unsigned long long t_br = VC_TRACE_NOW();
+            const long long t_am = VC_CYC();
             const int v = w.argmax(c);
+            VC_CYC_ADD(w, kPArgmax, t_am);
+            const long long t_store = VC_CYC();
             if (v < 0) {  // unreachable: m > 0 implies a live vertex of degree >= 1
                 if (w.tid == 0) raise_status(ctrl, VC_EINVAL);
                 stop = true;
@@ -498,7 +527,10 @@ __global__ void __launch_bounds__(WT, 1024 / WT) traverse_kernel(Params P) {
                     w.sync();
                 }
             }
+            VC_CYC_ADD(w, kPStore, t_store);
+            const long long t_tv = VC_CYC();
             w.take_vertex(c, v);
+            VC_CYC_ADD(w, kPTakeV, t_tv);
             VC_TRACE_ADD(w, kTBranchNs, t_br);
         }
     }
@@ -521,6 +553,7 @@ __global__ void __launch_bounds__(WT, 1024 / WT) traverse_kernel(Params P) {
         atomicAdd(&ctrl->trace_ns[2], T[kTBranchNs]);
         atomicAdd(&ctrl->trace_ns[3], T[kTSolutionNs]);
         atomicAdd(&ctrl->idle_polls, T[kTIdlePolls]);
+        for (int i = 0; i < kProfSlots; ++i) atomicAdd(&ctrl->trace_cycles[i], w.prof()[i]);
 #endif
         atomicMax(&ctrl->max_depth, (int32_t)T[kTMaxDepth]);
         if (P.sm_nodes) atomicAdd(&P.sm_nodes[smid() & (kSmSlots - 1)], T[kTNodes]);
@@ -531,10 +564,10 @@ __global__ void __launch_bounds__(WT, 1024 / WT) traverse_kernel(Params P) {
 // One node's reduction (tests): reads an int32 degree array, reduces it to the fixpoint in shared
 // memory (no early exit, like the oracle), writes it back with |S|, m and the stop verdict.
 // ------------------------------------------------------------------------------------------------
-template <typename W, int WT, bool GM>
+template <typename W, int WT, bool GM, int NW>
 __global__ void __launch_bounds__(WT) reduce_node_kernel(ReduceParams R) {
     extern __shared__ __align__(16) uint8_t smem[];
-    Worker<W, WT, GM> w(smem, R.n, 0, R.gstate);
+    Worker<W, WT, GM, NW> w(smem, R.n, 0, R.gstate);
     w.init_scratch(R.n);
     Ctx c;
     c.off = R.offsets;
@@ -545,6 +578,7 @@ __global__ void __launch_bounds__(WT) reduce_node_kernel(ReduceParams R) {
     c.kind = R.problem;
     c.k = R.bound;
     c.index = 0;
+    if constexpr (NW > 0) w.stage(c, nullptr, true);  // bit rows built from the CSR
     for (int v = w.tid; v < R.n; v += WT) w.d[v] = (W)R.deg[v];  // plain stores; read after sync()
     if (R.branch == -1) w.dirty_all(R.n);  // a state from outside: every vertex is looked at
     if (w.tid == 0) {
@@ -554,6 +588,7 @@ __global__ void __launch_bounds__(WT) reduce_node_kernel(ReduceParams R) {
         w.hdr->branch = -1;
     }
     w.sync();
+    if constexpr (NW > 0) w.init_live(c);
     // A branch from a fixpoint state starts clean, like a stored node in the traversal.
     if (R.branch >= 0) w.take_vertex(c, R.branch);
     else if (R.branch <= -2) w.take_neighbourhood(c, -2 - R.branch);

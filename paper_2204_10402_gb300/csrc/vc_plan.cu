@@ -35,7 +35,7 @@ using namespace vc;
 struct vc_plan {
     int32_t G = 0;
     int64_t total_vertices = 0;
-    int width = 16, wt = 32, smem = 0, workers = 0, eb = 0, cap = 0;
+    int width = 16, wt = 32, smem = 0, workers = 0, eb = 0, cap = 0, nw = 0;
     void *mem = nullptr;
     Problem *pristine = nullptr, *probs = nullptr;
     Control *ctrl = nullptr;
@@ -97,7 +97,14 @@ int vc_plan_create_mvc_batch(int32_t G, const int32_t *vtx, const int32_t *edge,
     pl->wt = cfg.worker_threads ? cfg.worker_threads : tuned.worker_threads;
     const int32_t csr_words = default_csr_words(n_max, cfg.stage_csr);
     pl->smem = smem_bytes_for(n_max, pl->width / 8, csr_words);
-    const Launchers &L = pl->width == 16 ? launchers_w16() : launchers_w32();
+    // Bit-row workers as in vc_mvc_batch: one warp per worker and n_max <= 128.
+    pl->nw = (cfg.bit_rows >= 0 && pl->wt == 32) ? rows_words_for(n_max) : 0;
+    if (cfg.bit_rows > 0 && pl->nw == 0) {
+        delete pl;
+        return VC_EINVAL;
+    }
+    pl->smem += rows_bytes_for(n_max, pl->nw);
+    const Launchers &L = launchers(pl->width, false, pl->nw);
     int per_sm = 0;
     if (pl->smem > (int)prop.sharedMemPerBlockOptin || L.occupancy(pl->wt, pl->smem, &per_sm) != VC_OK || per_sm <= 0) {
         delete pl;
@@ -134,6 +141,7 @@ int vc_plan_create_mvc_batch(int32_t G, const int32_t *vtx, const int32_t *edge,
     const size_t o_seq = take(sizeof(uint32_t) * cap);
     const size_t o_wl = take((size_t)cap * pl->eb);
     const size_t o_stk = take((size_t)pl->workers * (size_t)depth * pl->eb);
+    const size_t o_rows = take(sizeof(uint32_t) * (size_t)pl->nw * (size_t)std::max<int64_t>(total_v, 1));
     if (cudaMalloc(&pl->mem, off) != cudaSuccess) {
         cudaGetLastError();
         delete pl;
@@ -187,6 +195,7 @@ int vc_plan_create_mvc_batch(int32_t G, const int32_t *vtx, const int32_t *edge,
     P.idle_timeout_ns = cfg.idle_timeout_ns > 0 ? cfg.idle_timeout_ns : 20000000000ll;
     P.cancel = cfg.cancel;
     P.sm_nodes = reinterpret_cast<unsigned long long *>(b + o_smn);
+    P.rows = pl->nw > 0 ? reinterpret_cast<uint32_t *>(b + o_rows) : nullptr;
     if (rc == VC_OK && (cudaEventCreate(&pl->ev0) != cudaSuccess || cudaEventCreate(&pl->ev1) != cudaSuccess)) rc = VC_ECUDA;
     if (rc == VC_OK && cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) rc = VC_ECUDA;
     if (rc == VC_OK) {
@@ -250,10 +259,12 @@ int vc_plan_results(vc_plan *pl, void *stream, int32_t *sizes_out, int32_t *cove
         stats->entry_bytes_moved = (int64_t)c.entry_bytes;
         for (int i = 0; i < 4; ++i) stats->trace_ns[i] = (int64_t)c.trace_ns[i];
         stats->idle_polls = (int64_t)c.idle_polls;
+        for (int i = 0; i < 16; ++i) stats->trace_cycles[i] = (int64_t)c.trace_cycles[i];
         stats->max_depth = c.max_depth;
         stats->workers = pl->workers;
         stats->worker_threads = pl->wt;
         stats->width = pl->width;
+        stats->bit_rows = pl->nw;
         stats->status = c.status;
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, pl->ev0, pl->ev1) == cudaSuccess) stats->kernel_ms = ms;

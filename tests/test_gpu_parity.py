@@ -60,10 +60,12 @@ def test_rule_golden_cases(vc):
             assert got == want, (case["name"], width, got, want)
 
 
-@pytest.mark.parametrize("wt", [32, 64, 256])
-def test_reduce_node_random_states(vc, wt):
+@pytest.mark.parametrize("wt,bit_rows", [(32, 1), (32, -1), (64, 0), (256, 0)])
+def test_reduce_node_random_states(vc, wt, bit_rows):
+    # bit_rows = 1: adjacency bit rows (graphs up to 128 vertices; larger ones use CSR walks)
     rng_graphs = small_graphs(40, 20000, 10, 150)
     for i, g in enumerate(rng_graphs):
+        rows = bit_rows if (bit_rows <= 0 or g.n <= 128) else 0
         # a random intermediate state: remove a seeded subset, then reduce from there
         u = G.uniform01(30000 + i, g.n)
         removed = u < 0.15
@@ -84,7 +86,7 @@ def test_reduce_node_random_states(vc, wt):
             for rules in (1, 2, 4, 7):
                 want = oracle.reduce_node(g, deg, S, m, problem, bound, rules)
                 got = vc.reduce_node(g.offsets, g.neighbors, deg, S, m, problem, bound, rules,
-                                     config=vc.make_config(worker_threads=wt))
+                                     config=vc.make_config(worker_threads=wt, bit_rows=rows))
                 assert got[0].tolist() == want[0].tolist(), (i, problem, rules)
                 assert got[1:] == want[1:], (i, problem, rules, got[1:], want[1:])
 
@@ -134,12 +136,14 @@ def test_pvc_around_minimum(vc):
                 check_cover(g, a.cover, a.cover_size)
 
 
-@pytest.mark.parametrize("width,wt", [(16, 32), (32, 32), (16, 128), (32, 64), (16, 512)])
-def test_variants_agree(vc, width, wt):
+@pytest.mark.parametrize("width,wt,bit_rows", [(16, 32, 0), (32, 32, 0), (16, 32, -1), (32, 32, -1),
+                                               (16, 128, 0), (32, 64, 0), (16, 512, 0)])
+def test_variants_agree(vc, width, wt, bit_rows):
     for g in small_graphs(12, 70000, 30, 90):
         want, _, _ = oracle.mvc(g)
-        a = vc.mvc(g.offsets, g.neighbors, config=vc.make_config(width=width, worker_threads=wt))
+        a = vc.mvc(g.offsets, g.neighbors, config=vc.make_config(width=width, worker_threads=wt, bit_rows=bit_rows))
         assert a.value == want
+        assert a.stats["bit_rows"] == (0 if bit_rows < 0 or wt > 32 else (2 if g.n <= 64 else 4) if g.n > 32 else 1)
         check_cover(g, a.cover, want)
 
 
@@ -260,6 +264,18 @@ def test_batch_matches_oracle(vc):
     assert st["nodes_visited"] > 0
 
 
+@pytest.mark.parametrize("bit_rows", [1, -1])
+def test_batch_adjacency_modes_match_stored_answers(vc, bit_rows):
+    # The bench batch's first 512 graphs with bit rows forced on and off.
+    b = G.batch_gnp(512)
+    want = load_batch_golden()
+    sizes, covers, st = vc.mvc_batch(b.vtx, b.edge, b.offsets, b.neighbors, config=vc.make_config(bit_rows=bit_rows))
+    assert st["bit_rows"] == (4 if bit_rows > 0 else 0)
+    for i, g in enumerate(b.graphs):
+        assert sizes[i] == want[i][2], i
+        check_cover(g, covers[b.vtx[i]: b.vtx[i + 1]], want[i][2])
+
+
 def load_batch_golden():
     import os
     rows = {}
@@ -307,12 +323,12 @@ def _remove(g, deg, S, m, vertices):
     return deg, S + len(chosen), m
 
 
-@pytest.mark.parametrize("wt", [32, 128])
-def test_reduce_after_branch_matches_full_reduction(vc, wt):
+@pytest.mark.parametrize("wt,bit_rows", [(32, 0), (32, -1), (128, 0)])
+def test_reduce_after_branch_matches_full_reduction(vc, wt, bit_rows):
     # The traversal re-examines only vertices whose degree changed after a branch.  From a fixpoint
     # state, put v (or N(v)) into S and reduce: the result must equal the oracle's full reduction
     # of the same child state.
-    cfg = vc.make_config(worker_threads=wt)
+    cfg = vc.make_config(worker_threads=wt, bit_rows=bit_rows)
     for i, g in enumerate(small_graphs(30, 110000, 20, 150)):
         for problem, slack in ((oracle.MVC, 40), (oracle.PVC, 30)):
             bound = min(g.n, int(0.6 * g.n) + slack % 7)
