@@ -39,6 +39,7 @@ enum : int {
     kScB3 = 5,
     kScB4 = 6,
     kScB5 = 7,
+    kScWlHint = 40, // worklist fill seen by the node's snapshot
     kScKeys = 48,   // 16 x u64 per-warp argmax keys (words 48..79)
 };
 
@@ -414,10 +415,11 @@ struct Worker {
 
     // Points c at a shared-memory copy of its graph's offsets -- and of its neighbour lists too
     // when the launch reserved room for them -- copied when the problem changes.  Bit-row
-    // workers also load the graph's bit rows: from `grows` (global, written by the greedy pass)
-    // unless `build` is set or grows is null, in which case they are built from the CSR (and
-    // written to grows when it is given).
-    __device__ void stage(Ctx &c, uint32_t *grows = nullptr, bool build = true) {
+    // workers also load the graph's bit rows: BUILD = true builds them from the CSR (and writes
+    // them to `grows` when it is given); BUILD = false copies them from `grows`, where the
+    // greedy pass left them (the traversal, which then carries no build code).
+    template <bool BUILD = true>
+    __device__ void stage(Ctx &c, uint32_t *grows = nullptr) {
         const int n1 = c.n + 1;
         const bool copy_csr = csr_words > 0 && n1 <= csr_words;
         if (NW == 0 && !copy_csr) return;  // nothing to stage: read global memory
@@ -437,7 +439,7 @@ struct Worker {
             if (full)
                 for (int i = tid; i < len; i += WT) csr[n1 + i] = c.adj[i];
         }
-        if constexpr (NW > 0) stage_rows(c, grows, build);
+        if constexpr (NW > 0) stage_rows<BUILD>(c, grows);
         staged = c.index;
         staged_full = full;
         sync();
@@ -448,10 +450,16 @@ struct Worker {
     }
 
     // Bit rows of the graph (lane-parallel: lane handles vertices lane, lane+32, ...).
-    __device__ void stage_rows(const Ctx &c, uint32_t *grows, bool build) {
+    template <bool BUILD>
+    __device__ void stage_rows(const Ctx &c, uint32_t *grows) {
         using V = typename RowVec<kNW>::type;
         V *r = reinterpret_cast<V *>(rows);
-        if (!build && grows) {
+        if constexpr (!BUILD) {
+            if (!grows) {  // the host always gives bit-row traversals their rows
+                if (lane == 0 && dbg) raise_status(dbg, VC_EINVAL);
+                for (int v = lane; v < c.n; v += 32) r[v] = V{};  // empty rows until the launch stops
+                return;
+            }
             const V *g = reinterpret_cast<const V *>(grows);
             for (int v = lane; v < c.n; v += 32) r[v] = __ldcg(g + v);
             return;
@@ -479,8 +487,10 @@ struct Worker {
         RowVec<kNW>::unpack(reinterpret_cast<const typename RowVec<kNW>::type *>(rows)[v], b);
     }
     __device__ __forceinline__ void live_words(uint32_t (&b)[kNW]) const {
-#pragma unroll
-        for (int w = 0; w < NW; ++w) b[w] = livew[w];
+        RowVec<kNW>::unpack(*reinterpret_cast<const typename RowVec<kNW>::type *>(livew), b);
+    }
+    __device__ __forceinline__ void chosen_words(uint32_t (&b)[kNW]) const {
+        RowVec<kNW>::unpack(*reinterpret_cast<const typename RowVec<kNW>::type *>(newm), b);
     }
     // Lowest set bit over NW words, or -1.
     static __device__ __forceinline__ int first_bit(const uint32_t (&b)[kNW]) {
@@ -505,7 +515,7 @@ struct Worker {
 
     // Live mask of the current node from its degree array (after a node is loaded).
     __device__ void init_live(const Ctx &c) {
-#pragma unroll
+#pragma unroll 1
         for (int k = 0; k < NW; ++k) {
             const int v = 32 * k + lane;
             const unsigned m = __ballot_sync(kFull, v < c.n && deg(v) != -1);
@@ -621,65 +631,89 @@ struct Worker {
 
     // Moves the chosen set newm into S: every live vertex outside it gets its degree recomputed as
     // popc(row & live'), a vertex whose degree changed is marked dirty for both passes, and
-    // m = (sum of live degrees) / 2.  Same result as apply_list's decrements.
+    // m = (sum of live degrees) / 2.  Same result as apply_list's decrements.  (The loops over
+    // 32-vertex chunks are kept rolled and read the chunk's mask words from shared memory: the
+    // traversal is sensitive to its code size.)
     __device__ void apply_rows(const Ctx &c) {
         __syncwarp();  // every proposal (shared atomics) is done
-        uint32_t rm[kNW], nl[kNW];
-        int cnt = 0;
+        uint32_t nl[kNW];
+        live_words(nl);
+        int cnt = 0, u = -1;
 #pragma unroll
         for (int w = 0; w < NW; ++w) {
-            rm[w] = newm[w];
-            nl[w] = livew[w] & ~rm[w];
-            cnt += __popc(rm[w]);
+            const uint32_t rw = newm[w];
+            nl[w] &= ~rw;
+            cnt += __popc(rw);
+            if (u < 0 && rw) u = 32 * w + __ffs(rw) - 1;
         }
-        int degsum = 0, words = 0;
+        const int chunks = (c.n + 31) >> 5;
+        if (cnt == 1) {
+            // One vertex u (the "v" child, most single rule removals): its live neighbours lose
+            // one degree each and are exactly the vertices whose degree changes; m loses deg(u).
+            const int du = deg(u);
+            const uint32_t *ru = rows + u * NW;
+#pragma unroll 1
+            for (int k = 0; k < chunks; ++k) {
+                const uint32_t hit = ru[k] & livew[k];  // u itself has no self-loop bit
+                const int v = 32 * k + lane;
+                if ((hit >> lane) & 1u) d[v] = (W)(deg(v) - 1);
+                if (lane == 0 && hit) dirty[k] |= (unsigned long long)hit * 0x100000001ull;
+            }
+            if (lane == 0) {
+                d[u] = (W)-1;
+                hdr->S += 1;
+                hdr->m -= du;
+                tally[kTCsr] += (unsigned long long)(c.off[u + 1] - c.off[u]);
+            }
+        } else {
+            int degsum = 0, words = 0;
+#pragma unroll 1
+            for (int k = 0; k < chunks; ++k) {
+                const int v = 32 * k + lane;
+                bool changed = false;
+                if (v < c.n) {
+                    const int dv = deg(v);
+                    if ((newm[k] >> lane) & 1u) {
+                        d[v] = (W)-1;
+                        words += c.off[v + 1] - c.off[v];
+                    } else if (dv >= 0) {
+                        uint32_t b[kNW];
+                        row(v, b);
+                        int nd = 0;
 #pragma unroll
-        for (int k = 0; k < NW; ++k) {
-            const int v = 32 * k + lane;
-            bool changed = false;
-            if (v < c.n) {
-                const int dv = deg(v);
-                if ((rm[k] >> lane) & 1u) {
-                    d[v] = (W)-1;
-                    words += c.off[v + 1] - c.off[v];
-                } else if (dv >= 0) {
-                    uint32_t b[kNW];
-                    row(v, b);
-                    int nd = 0;
-#pragma unroll
-                    for (int w = 0; w < NW; ++w) nd += __popc(b[w] & nl[w]);
-                    if (nd != dv) {
-                        d[v] = (W)nd;
-                        changed = true;
+                        for (int w = 0; w < NW; ++w) nd += __popc(b[w] & nl[w]);
+                        if (nd != dv) {
+                            d[v] = (W)nd;
+                            changed = true;
+                        }
+                        degsum += nd;
                     }
-                    degsum += nd;
                 }
+                const unsigned chg = __ballot_sync(kFull, changed);
+                if (lane == 0 && chg) dirty[k] |= (unsigned long long)chg * 0x100000001ull;
             }
-            const unsigned chg = __ballot_sync(kFull, changed);
-            if (lane == 0 && chg) dirty[k] |= (unsigned long long)chg * 0x100000001ull;
+            degsum = __reduce_add_sync(kFull, degsum);
+            words = __reduce_add_sync(kFull, words);
+            if (lane == 0) {
+                hdr->S += cnt;
+                hdr->m = degsum / 2;
+                tally[kTCsr] += (unsigned long long)words;
+            }
         }
-        degsum = __reduce_add_sync(kFull, degsum);
-        words = __reduce_add_sync(kFull, words);
+        __syncwarp();  // every lane has read newm and livew
         if (lane == 0) {
-            hdr->S += cnt;
-            hdr->m = degsum / 2;
-#pragma unroll
-            for (int w = 0; w < NW; ++w) {
-                livew[w] = nl[w];
-                newm[w] = 0u;
-            }
-            tally[kTCsr] += (unsigned long long)words;
+            using V = typename RowVec<kNW>::type;
+            *reinterpret_cast<V *>(livew) = RowVec<kNW>::pack(nl);
+            *reinterpret_cast<V *>(newm) = V{};
         }
         __syncwarp();
     }
 
     // Ends a bit-row scan: returns whether any lane chose a vertex (the choice waits in newm).
-    __device__ __forceinline__ bool rows_finish(bool proposed, int words, int slot, long long t0) {
-        words = __reduce_add_sync(kFull, words);
-        if (lane == 0) {
-            tally[kTPasses] += 1;
-            tally[kTCsr] += (unsigned long long)words;
-        }
+    // (Bit-row scans walk no CSR; csr_words counts the removals' adjacency lists, the part of the
+    // algorithmic traffic that every implementation reads.)
+    __device__ __forceinline__ bool rows_finish(bool proposed, int slot, long long t0) {
+        if (lane == 0) tally[kTPasses] += 1;
         const bool any = __any_sync(kFull, proposed);
         VC_CYC_ADD(*this, slot, t0);
         VC_CYC_INC(*this, slot + (kPDeg1Count - kPDeg1));
@@ -690,70 +724,63 @@ struct Worker {
     // row(v) & live (one lane per vertex; same tie-break as pass_degree_one).
     __device__ bool rows_pass_degree_one(const Ctx &c) {
         const long long t0 = VC_CYC();
-        uint32_t lv[kNW];
-        live_words(lv);
         bool proposed = false;
-        int words = 0;
+        const int chunks = (c.n + 31) >> 5;
 #pragma unroll
         for (int k = 0; k < NW; ++k) {
-            if (32 * k >= c.n) break;
+            if (k >= chunks) break;
             const unsigned long long dw = dirty[k];
             const unsigned bits = (unsigned)dw;
             if (bits == 0u) continue;
             if (lane == 0) dirty[k] = dw & 0xffffffff00000000ull;
             const int v = 32 * k + lane;
             if (((bits >> lane) & 1u) && v < c.n && deg(v) == 1) {
-                uint32_t b[kNW];
+                uint32_t b[kNW], lv[kNW];
                 row(v, b);
+                live_words(lv);
 #pragma unroll
                 for (int w = 0; w < NW; ++w) b[w] &= lv[w];
                 const int u = first_bit(b);
-                words += c.off[v + 1] - c.off[v];
                 if (u >= 0 && !(deg(u) == 1 && u > v)) {
                     atomicOr(&newm[u >> 5], 1u << (u & 31));
                     proposed = true;
                 }
             }
         }
-        return rows_finish(proposed, words, kPDeg1, t0);
+        return rows_finish(proposed, kPDeg1, t0);
     }
 
     // Degree-two-triangle over bit rows: the two lowest bits of row(v) & live are u < w, and uw is
     // an edge iff bit w of row(u) is set (same tie-break as pass_degree_two_triangle).
     __device__ bool rows_pass_degree_two_triangle(const Ctx &c) {
         const long long t0 = VC_CYC();
-        uint32_t lv[kNW];
-        live_words(lv);
         bool proposed = false;
-        int words = 0;
+        const int chunks = (c.n + 31) >> 5;
 #pragma unroll
         for (int k = 0; k < NW; ++k) {
-            if (32 * k >= c.n) break;
+            if (k >= chunks) break;
             const unsigned long long dw = dirty[k];
             const unsigned bits = (unsigned)(dw >> 32);
             if (bits == 0u) continue;
             if (lane == 0) dirty[k] = dw & 0xffffffffull;
             const int v = 32 * k + lane;
             if (((bits >> lane) & 1u) && v < c.n && deg(v) == 2) {
-                uint32_t b[kNW];
+                uint32_t b[kNW], lv[kNW];
                 row(v, b);
+                live_words(lv);
 #pragma unroll
                 for (int w = 0; w < NW; ++w) b[w] &= lv[w];
                 const int u = first_bit(b);
                 clear_first(b);
                 const int x = first_bit(b);
-                words += c.off[v + 1] - c.off[v];
-                if (u >= 0 && x >= 0) {
-                    words += min(c.off[u + 1] - c.off[u], c.off[x + 1] - c.off[x]);
-                    if (row_has(u, x) && !((deg(u) == 2 && u < v) || (deg(x) == 2 && x < v))) {
-                        atomicOr(&newm[u >> 5], 1u << (u & 31));
-                        atomicOr(&newm[x >> 5], 1u << (x & 31));
-                        proposed = true;
-                    }
+                if (u >= 0 && x >= 0 && row_has(u, x) && !((deg(u) == 2 && u < v) || (deg(x) == 2 && x < v))) {
+                    atomicOr(&newm[u >> 5], 1u << (u & 31));
+                    atomicOr(&newm[x >> 5], 1u << (x & 31));
+                    proposed = true;
                 }
             }
         }
-        return rows_finish(proposed, words, kPTri, t0);
+        return rows_finish(proposed, kPTri, t0);
     }
 
     // High-degree over the lanes' own vertices: one ballot per 32 vertices.
@@ -761,16 +788,17 @@ struct Worker {
         const long long t0 = VC_CYC();
         const int thr = (c.kind == kMVC) ? bound - hdr->S - 1 : bound - hdr->S;
         bool proposed = false;
+        const int chunks = (c.n + 31) >> 5;
 #pragma unroll
         for (int k = 0; k < NW; ++k) {
-            if (32 * k >= c.n) break;
+            if (k >= chunks) break;
             const int v = 32 * k + lane;
             const int dv = v < c.n ? deg(v) : -1;
             const unsigned m = __ballot_sync(kFull, dv != -1 && dv > thr);
             if (lane == 0) newm[k] = m;
             proposed |= m != 0u;
         }
-        return rows_finish(proposed, 0, kPHigh, t0);
+        return rows_finish(proposed, kPHigh, t0);
     }
 
     // Ends a scan: returns whether some thread proposed a vertex (the proposals wait in the
@@ -787,9 +815,11 @@ struct Worker {
     // a barrier).
     __device__ __forceinline__ bool has_pending() const {
         if constexpr (NW > 0) {
+            uint32_t b[kNW];
+            chosen_words(b);
             bool any = false;
 #pragma unroll
-            for (int w = 0; w < NW; ++w) any |= newm[w] != 0u;
+            for (int w = 0; w < NW; ++w) any |= b[w] != 0u;
             return any;
         } else {
             return sc[kScCount] != 0;

@@ -53,7 +53,7 @@ __device__ bool greedy_solve(const Params &P, Worker<W, WT, GM, NW> &w, Ctx &c) 
         w.sync();
         return false;
     }
-    w.stage(c, rows_of<NW>(P, c), true);
+    w.stage(c, rows_of<NW>(P, c));
     w.load_root(c);
     const int32_t m0 = w.hdr->m;
     for (;;) {
@@ -129,10 +129,12 @@ __device__ __forceinline__ bool wait_seq(const Params &P, uint32_t slot, uint32_
 }
 
 // Producer side: a ticket whose slot is ready for writing, or -1 (worklist at its threshold or
-// full: the caller pushes on its local stack instead), or -2 (timed out).
-__device__ __forceinline__ long long wl_reserve(const Params &P) {
+// full: the caller pushes on its local stack instead), or -2 (timed out).  `fill` is the
+// worklist count the caller saw (read with the node's snapshot, so that the threshold test costs
+// no extra round trip to L2; the free-slot reservation below is what bounds the ring).
+__device__ __forceinline__ long long wl_reserve(const Params &P, int32_t fill) {
     Control *c = P.ctrl;
-    if (ld_relaxed(&c->wl_count) >= P.wl_threshold) return -1;
+    if (fill >= P.wl_threshold) return -1;
     if (atomicSub(&c->wl_space, 1) <= 0) {
         atomicAdd(&c->wl_space, 1);
         return -1;
@@ -429,7 +431,7 @@ __global__ void __launch_bounds__(WT, 1024 / WT) traverse_kernel(Params P) {
                 c = make_ctx(P, cur);
                 VC_CHECK(ctrl, c.n >= 0 && c.n <= P.n_max, 14, c.n, { stop = true; break; });
                 w.cur_n = c.n;
-                w.stage(c, rows_of<NW>(P, c), false);
+                w.template stage<false>(c, rows_of<NW>(P, c));
                 if constexpr (NW > 0) w.init_live(c);
             }
         }
@@ -449,6 +451,7 @@ __global__ void __launch_bounds__(WT, 1024 / WT) traverse_kernel(Params P) {
                 w.sc[kScB0] = (c.kind == kMVC) ? ld_relaxed(&c.prob->best) : c.k;
                 w.sc[kScB1] = (c.kind == kPVC) ? ld_relaxed(&c.prob->found) : 0;
                 w.sc[kScB2] = ld_relaxed(&ctrl->status);
+                w.sc[kScWlHint] = ld_relaxed(&ctrl->wl_count);
             }
             w.sync();
             const int32_t bound = w.sc[kScB0];  // one snapshot of best per node (reading R3)
@@ -493,7 +496,7 @@ __global__ void __launch_bounds__(WT, 1024 / WT) traverse_kernel(Params P) {
             const bool keep = (c.kind == kMVC) ? (S + dv < bound) : (S + dv <= c.k);
             if (keep) {
                 if (w.tid == 0) {
-                    const long long pos = wl_reserve(P);
+                    const long long pos = wl_reserve(P, w.sc[kScWlHint]);
                     w.sc[kScB3] = pos >= 0;
                     w.sc[kScB4] = (int32_t)(uint32_t)(pos >= 0 ? pos : 0);
                 }
@@ -578,7 +581,7 @@ __global__ void __launch_bounds__(WT) reduce_node_kernel(ReduceParams R) {
     c.kind = R.problem;
     c.k = R.bound;
     c.index = 0;
-    if constexpr (NW > 0) w.stage(c, nullptr, true);  // bit rows built from the CSR
+    if constexpr (NW > 0) w.stage(c, nullptr);  // bit rows built from the CSR
     for (int v = w.tid; v < R.n; v += WT) w.d[v] = (W)R.deg[v];  // plain stores; read after sync()
     if (R.branch == -1) w.dirty_all(R.n);  // a state from outside: every vertex is looked at
     if (w.tid == 0) {
