@@ -84,10 +84,10 @@ typedef struct {
                                    vc_mvc, vc_pvc, vc_mvc_batch, vc_greedy and vc_reduce_node honour it;
                                    the server, the batch plan and vc_mvc_noalloc keep the node in shared
                                    memory. */
-    int32_t bit_rows;           /* adjacency lookups of one-warp, shared-memory workers on graphs of at most
-                                   128 vertices: 0 = bit rows of the adjacency matrix in shared memory when
-                                   the launch qualifies, else CSR walks; 1 = bit rows (VC_EINVAL when the
-                                   launch does not qualify); -1 = CSR walks.  Same answers and reduced
+    int32_t bit_rows;           /* adjacency lookups of one-warp, shared-memory workers: 0 = bit rows of the
+                                   adjacency matrix in shared memory for graphs of at most 128 vertices,
+                                   else CSR walks; 1 = bit rows, also for graphs of up to 256 vertices
+                                   (VC_EINVAL when the launch does not qualify); -1 = CSR walks.  Same answers and reduced
                                    degree arrays either way.  vc_mvc, vc_pvc, vc_mvc_batch, vc_greedy,
                                    vc_reduce_node and the batch plan honour it; the server and
                                    vc_mvc_noalloc walk the CSR. */

@@ -228,12 +228,14 @@ static_assert(kScProf + 2 * kProfSlots <= kScratchWords, "profile slots exceed t
     } while (0)
 #endif
 
-// NW-word bit rows as one vector load / store.
+// NW-word bit rows as one vector load / store (two 16-byte halves for 8 words).
 template <int NW> struct RowVec;
 template <> struct RowVec<1> {
     using type = uint32_t;
     static __device__ __forceinline__ type pack(const uint32_t (&b)[1]) { return b[0]; }
     static __device__ __forceinline__ void unpack(type q, uint32_t (&b)[1]) { b[0] = q; }
+    static __device__ __forceinline__ type load_cg(const type *p) { return __ldcg(p); }
+    static __device__ __forceinline__ void store_cg(type *p, type q) { __stcg(p, q); }
 };
 template <> struct RowVec<2> {
     using type = uint2;
@@ -242,6 +244,8 @@ template <> struct RowVec<2> {
         b[0] = q.x;
         b[1] = q.y;
     }
+    static __device__ __forceinline__ type load_cg(const type *p) { return __ldcg(p); }
+    static __device__ __forceinline__ void store_cg(type *p, type q) { __stcg(p, q); }
 };
 template <> struct RowVec<4> {
     using type = uint4;
@@ -251,6 +255,32 @@ template <> struct RowVec<4> {
         b[1] = q.y;
         b[2] = q.z;
         b[3] = q.w;
+    }
+    static __device__ __forceinline__ type load_cg(const type *p) { return __ldcg(p); }
+    static __device__ __forceinline__ void store_cg(type *p, type q) { __stcg(p, q); }
+};
+struct alignas(16) Row8 {
+    uint4 lo, hi;
+};
+template <> struct RowVec<8> {
+    using type = Row8;
+    static __device__ __forceinline__ type pack(const uint32_t (&b)[8]) {
+        return Row8{make_uint4(b[0], b[1], b[2], b[3]), make_uint4(b[4], b[5], b[6], b[7])};
+    }
+    static __device__ __forceinline__ void unpack(const type &q, uint32_t (&b)[8]) {
+        b[0] = q.lo.x;
+        b[1] = q.lo.y;
+        b[2] = q.lo.z;
+        b[3] = q.lo.w;
+        b[4] = q.hi.x;
+        b[5] = q.hi.y;
+        b[6] = q.hi.z;
+        b[7] = q.hi.w;
+    }
+    static __device__ __forceinline__ type load_cg(const type *p) { return Row8{__ldcg(&p->lo), __ldcg(&p->hi)}; }
+    static __device__ __forceinline__ void store_cg(type *p, const type &q) {
+        __stcg(&p->lo, q.lo);
+        __stcg(&p->hi, q.hi);
     }
 };
 
@@ -269,10 +299,11 @@ template <> struct RowVec<4> {
 // degree arrays are the same as the CSR walks'.
 template <typename W, int WT, bool GM = false, int NW = 0>
 struct Worker {
-    static_assert(NW == 0 || NW == 1 || NW == 2 || NW == 4, "bit rows of 1, 2 or 4 words");
+    static_assert(NW == 0 || NW == 1 || NW == 2 || NW == 4 || NW == 8, "bit rows of 1, 2, 4 or 8 words");
     static_assert(NW == 0 || (WT == 32 && !GM), "bit rows are for one-warp shared-memory workers");
     static constexpr int kWarps = WT / 32;
     static constexpr int kNW = NW > 0 ? NW : 1;  // array extent for the bit-row helpers
+    static constexpr int kMaskWords = kNW > 4 ? kNW : 4;  // live / chosen masks, 16-byte multiples
     EntryHeader *hdr;
     W *d;
     uint32_t *marks;
@@ -307,6 +338,12 @@ struct Worker {
             dirty = reinterpret_cast<unsigned long long *>(g + mark_bytes);
             list = reinterpret_cast<int32_t *>(g + mark_bytes + dirty_bytes);
             sc = reinterpret_cast<int32_t *>(smem + 16);
+        } else if constexpr (NW > 0) {  // bit-row workers need no marks or removal list
+            d = reinterpret_cast<W *>(smem + 16);
+            marks = nullptr;
+            list = nullptr;
+            dirty = reinterpret_cast<unsigned long long *>(smem + eb);
+            sc = reinterpret_cast<int32_t *>(smem + eb + dirty_bytes);
         } else {
             d = reinterpret_cast<W *>(smem + 16);
             marks = reinterpret_cast<uint32_t *>(smem + eb);
@@ -319,8 +356,8 @@ struct Worker {
         csr = sc + kScratchWords;
         csr_words = csr_capacity;
         livew = reinterpret_cast<uint32_t *>(csr) + pad16((int64_t)csr_capacity * 4) / 4;
-        newm = livew + 4;
-        rows = livew + 8;
+        newm = livew + kMaskWords;
+        rows = livew + 2 * kMaskWords;
         staged = -1;
         staged_full = false;
         dbg = nullptr;
@@ -406,10 +443,12 @@ struct Worker {
     // Clears scratch state; call once per kernel before any pass.
     __device__ void init_scratch(int32_t n_max) {
         for (int i = tid; i < (n_max + 31) / 32; i += WT) {
-            marks[i] = 0;
+            if constexpr (NW == 0) marks[i] = 0;  // bit-row workers have no marks
             dirty[i] = 0ull;
         }
         for (int i = tid; i < kScratchWords; i += WT) sc[i] = 0;
+        if constexpr (NW > 0)
+            for (int i = tid; i < 2 * kMaskWords; i += WT) livew[i] = 0u;  // live and chosen masks
         sync();
     }
 
@@ -461,7 +500,7 @@ struct Worker {
                 return;
             }
             const V *g = reinterpret_cast<const V *>(grows);
-            for (int v = lane; v < c.n; v += 32) r[v] = __ldcg(g + v);
+            for (int v = lane; v < c.n; v += 32) r[v] = RowVec<kNW>::load_cg(g + v);
             return;
         }
         for (int v = lane; v < c.n; v += 32) {
@@ -477,7 +516,7 @@ struct Worker {
             }
             const V q = RowVec<kNW>::pack(b);
             r[v] = q;
-            if (grows) __stcg(reinterpret_cast<V *>(grows) + v, q);
+            if (grows) RowVec<kNW>::store_cg(reinterpret_cast<V *>(grows) + v, q);
         }
     }
 

@@ -215,9 +215,10 @@ int run(Workspace &ws, const Spec &spec, const vc_config *cfg_in, cudaStream_t s
     if (smem > ws.smem_optin) return VC_EINVAL;  // graph too large for a shared-memory degree array
     // Bit-row workers: one warp per worker, node in shared memory, n_max <= 128.
     int nw = 0;
-    if (cfg.bit_rows >= 0 && !gm && wt == 32) nw = rows_words_for(n_max);
+    if (cfg.bit_rows >= 0 && !gm && wt == 32) nw = rows_words_for(n_max, cfg.bit_rows > 0);
     if (cfg.bit_rows > 0 && nw == 0) return VC_EINVAL;
-    if (nw > 0 && smem + rows_bytes_for(n_max, nw) <= ws.smem_optin) smem += rows_bytes_for(n_max, nw);
+    if (nw > 0 && smem_bytes_for(n_max, wbytes, csr_words, nw) <= ws.smem_optin)
+        smem = smem_bytes_for(n_max, wbytes, csr_words, nw);
     else nw = 0;
     const Launchers &L = launchers(width, gm, nw);
     int per_sm = 0;
@@ -583,9 +584,9 @@ int vc_reduce_node(const vc_graph *g, int32_t *deg, int32_t *S, int32_t *m, int3
     const bool gm = c.node_in_global > 0 || (c.node_in_global == 0 && smem > ws->smem_optin);
     if (gm) smem = smem_bytes_gm(0);
     if (smem > ws->smem_optin) return VC_EINVAL;
-    int nw = (c.bit_rows >= 0 && !gm && wt == 32) ? rows_words_for(g->n) : 0;
+    int nw = (c.bit_rows >= 0 && !gm && wt == 32) ? rows_words_for(g->n, c.bit_rows > 0) : 0;
     if (c.bit_rows > 0 && nw == 0) return VC_EINVAL;
-    smem += rows_bytes_for(g->n, nw);
+    if (nw > 0) smem = smem_bytes_for(g->n, width / 8, 0, nw);
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t len = g->on_device ? -1 : g->offsets[g->n];
     // device copies: graph (if host), degree array, io words

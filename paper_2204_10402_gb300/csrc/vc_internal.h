@@ -150,13 +150,19 @@ VC_HD inline int32_t entry_bytes_for(int32_t n_max, int32_t width_bytes) {
 constexpr int kScratchWords = 112;
 // Per-SM node counters are indexed by %smid modulo this power of two.
 constexpr int kSmSlots = 1024;
-VC_HD inline int32_t smem_bytes_for(int32_t n_max, int32_t width_bytes, int32_t csr_words = 0) {
+VC_HD inline int32_t smem_bytes_for(int32_t n_max, int32_t width_bytes, int32_t csr_words = 0, int32_t nw = 0) {
     int64_t b = entry_bytes_for(n_max, width_bytes);
-    b += pad16(((int64_t)n_max + 31) / 32 * 4);  // marks
+    if (nw == 0) {
+        b += pad16(((int64_t)n_max + 31) / 32 * 4);  // marks
+        b += pad16((int64_t)n_max * 4);             // removal list
+    }
     b += pad16(((int64_t)n_max + 31) / 32 * 8);  // dirty bits (two per vertex)
-    b += pad16((int64_t)n_max * 4);             // removal list
     b += kScratchWords * 4;
     b += pad16((int64_t)csr_words * 4);         // staged CSR
+    if (nw > 0) {                                // bit-row workers: live and chosen masks, rows
+        const int64_t mask_bytes = (nw > 4 ? nw : 4) * 4;
+        b += 2 * mask_bytes + pad16((int64_t)n_max * nw * 4);
+    }
     return (int32_t)b;
 }
 
@@ -196,12 +202,13 @@ VC_HD inline int32_t default_worklist_capacity(int32_t entry_bytes) {
 VC_HD inline int32_t smem_bytes_gm(int32_t csr_words) {
     return 16 + kScratchWords * 4 + pad16((int64_t)csr_words * 4);
 }
-// Bit-row workers (NW = 1, 2 or 4 words per row, graphs of at most 32 * NW vertices): the live
-// mask and chosen set (16 B each) and n_max rows after the staged CSR.
-VC_HD inline int32_t rows_bytes_for(int32_t n_max, int32_t nw) {
-    return nw > 0 ? 32 + pad16((int64_t)n_max * nw * 4) : 0;
+// Bit-row workers: words per adjacency row for graphs of at most n_max vertices (0 = none).
+// By default only up to 4 words: on the planted-clique graphs (n = 160-200, p = 0.05) 8-word rows
+// ran 1.5-2.3x slower than CSR walks (sparse rows, and fewer workers fit), so they are used only
+// on request (`forced`).
+VC_HD inline int32_t rows_words_for(int32_t n_max, bool forced = false) {
+    return n_max <= 32 ? 1 : n_max <= 64 ? 2 : n_max <= 128 ? 4 : (forced && n_max <= 256) ? 8 : 0;
 }
-VC_HD inline int32_t rows_words_for(int32_t n_max) { return n_max <= 32 ? 1 : n_max <= 64 ? 2 : n_max <= 128 ? 4 : 0; }
 VC_HD inline int32_t gstate_bytes_for(int32_t n_max, int32_t width_bytes) {
     int64_t b = pad16((int64_t)n_max * width_bytes);
     b += pad16(((int64_t)n_max + 31) / 32 * 4);

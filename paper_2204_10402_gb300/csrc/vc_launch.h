@@ -1,7 +1,7 @@
 // vc_launch.h - host-side entry points into the templated kernels, one set per degree-array
 // width and node placement (vc_kern_w16.cu, vc_kern_w32.cu: node in shared memory;
 // vc_kern_w16_gm.cu, vc_kern_w32_gm.cu: node in global memory; vc_kern_w16_rows.cu,
-// vc_kern_w32_rows.cu: bit-row workers for graphs of at most 128 vertices).
+// vc_kern_w32_rows.cu: bit-row workers for graphs of at most 256 vertices).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -22,7 +22,7 @@ const Launchers &launchers_w16();
 const Launchers &launchers_w32();
 const Launchers &launchers_w16_gm();
 const Launchers &launchers_w32_gm();
-const Launchers &launchers_w16_rows(int nw);  // nw = 1, 2 or 4; one-warp workers only
+const Launchers &launchers_w16_rows(int nw);  // nw = 1, 2, 4 or 8; one-warp workers only
 const Launchers &launchers_w32_rows(int nw);
 inline const Launchers &launchers(int width, bool gm, int nw = 0) {
     if (nw > 0) return width == 16 ? launchers_w16_rows(nw) : launchers_w32_rows(nw);

@@ -98,12 +98,12 @@ int vc_plan_create_mvc_batch(int32_t G, const int32_t *vtx, const int32_t *edge,
     const int32_t csr_words = default_csr_words(n_max, cfg.stage_csr);
     pl->smem = smem_bytes_for(n_max, pl->width / 8, csr_words);
     // Bit-row workers as in vc_mvc_batch: one warp per worker and n_max <= 128.
-    pl->nw = (cfg.bit_rows >= 0 && pl->wt == 32) ? rows_words_for(n_max) : 0;
+    pl->nw = (cfg.bit_rows >= 0 && pl->wt == 32) ? rows_words_for(n_max, cfg.bit_rows > 0) : 0;
     if (cfg.bit_rows > 0 && pl->nw == 0) {
         delete pl;
         return VC_EINVAL;
     }
-    pl->smem += rows_bytes_for(n_max, pl->nw);
+    if (pl->nw > 0) pl->smem = smem_bytes_for(n_max, pl->width / 8, csr_words, pl->nw);
     const Launchers &L = launchers(pl->width, false, pl->nw);
     int per_sm = 0;
     if (pl->smem > (int)prop.sharedMemPerBlockOptin || L.occupancy(pl->wt, pl->smem, &per_sm) != VC_OK || per_sm <= 0) {

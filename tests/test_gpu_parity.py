@@ -62,10 +62,10 @@ def test_rule_golden_cases(vc):
 
 @pytest.mark.parametrize("wt,bit_rows", [(32, 1), (32, -1), (64, 0), (256, 0)])
 def test_reduce_node_random_states(vc, wt, bit_rows):
-    # bit_rows = 1: adjacency bit rows (graphs up to 128 vertices; larger ones use CSR walks)
-    rng_graphs = small_graphs(40, 20000, 10, 150)
+    # bit_rows = 1: adjacency bit rows (graphs up to 256 vertices; larger ones use CSR walks)
+    rng_graphs = small_graphs(40, 20000, 10, 250)
     for i, g in enumerate(rng_graphs):
-        rows = bit_rows if (bit_rows <= 0 or g.n <= 128) else 0
+        rows = bit_rows if (bit_rows <= 0 or g.n <= 256) else 0
         # a random intermediate state: remove a seeded subset, then reduce from there
         u = G.uniform01(30000 + i, g.n)
         removed = u < 0.15
@@ -408,14 +408,16 @@ def test_planted_clique_pvc_three_columns(vc):
             assert a.cover_size <= k
 
 
-@pytest.mark.parametrize("n", [180, 200])
-def test_planted_clique_stored_answers(vc, n):
-    # Sizes the oracle needs minutes for (answers stored by tests/golden/make_clique_golden.py).
+@pytest.mark.parametrize("n,bit_rows", [(180, 1), (200, 0), (180, -1)])
+def test_planted_clique_stored_answers(vc, n, bit_rows):
+    # Sizes the oracle needs minutes for (answers stored by tests/golden/make_clique_golden.py);
+    # 8-word bit rows on request (bit_rows = 1), CSR walks by default and with bit_rows = -1.
     c, m, want = load_clique_golden()[n]
     g, _ = G.gnp_with_planted_clique(n, 0.05, c, 0)
     assert g.m == m
-    a = vc.mvc(g.offsets, g.neighbors)
+    a = vc.mvc(g.offsets, g.neighbors, config=vc.make_config(bit_rows=bit_rows))
     assert a.value == want
+    assert a.stats["bit_rows"] == (8 if bit_rows == 1 else 0)
     check_cover(g, a.cover, want)
     assert vc.pvc(g.offsets, g.neighbors, want - 1, want_cover=False).value == 0
 
