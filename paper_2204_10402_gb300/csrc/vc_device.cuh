@@ -363,9 +363,10 @@ struct Worker {
         dbg = nullptr;
         cur_n = n_max;
         n_cap = n_max;
-        tid = threadIdx.x;
+        // One-warp workers: tid < 32 and warp = 0 are compile-time facts for the code generator.
+        tid = (WT == 32) ? (int)(threadIdx.x & 31) : (int)threadIdx.x;
         lane = tid & 31;
-        warp = tid >> 5;
+        warp = (WT == 32) ? 0 : tid >> 5;
         entry_bytes = eb;
     }
 

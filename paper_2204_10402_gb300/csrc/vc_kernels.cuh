@@ -369,12 +369,19 @@ __device__ int acquire(const Params &P, Worker<W, WT, GM, NW> &w) {
 // ------------------------------------------------------------------------------------------------
 // Persistent hybrid traversal (Sec. IV-A): one worker per thread block.
 // ------------------------------------------------------------------------------------------------
-// At most 64 registers per thread, so every worker size keeps 2048 threads resident per SM
+// At most 64 registers per thread, so every worker size keeps 1024 threads resident per SM
 // (measured: the uncapped build used 72 registers, fit 28 one-warp blocks per SM and ran 4 % slower).
+// One-warp workers declare 64 threads / 16 blocks, the same 64-register cap; with the worker's
+// compile-time warp indices this build ran the 4096-graph batch in 174 ms against 180 ms for
+// (32, 32) on one GB300.  More resident warps did not pay: 48, 40 and 32 registers with two or
+// four workers per block (40 to 64 warps per SM) ran 171, 180 and 250 ms against 171 ms for the
+// same build at 64 registers.
+constexpr int kMaxThreads(int wt) { return wt == 32 ? 64 : wt; }
+constexpr int kMinBlocks(int wt) { return wt == 32 ? 16 : 1024 / wt; }
 // SERVE: the launch also takes requests from a server's ring (the instance the server launches);
 // batch launches use the instance without that path, which keeps their code smaller.
 template <typename W, int WT, bool GM, int NW, bool SERVE>
-__global__ void __launch_bounds__(WT, 1024 / WT) traverse_kernel(Params P) {
+__global__ void __launch_bounds__(kMaxThreads(WT), kMinBlocks(WT)) traverse_kernel(Params P) {
     extern __shared__ __align__(16) uint8_t smem[];
     Worker<W, WT, GM, NW> w(smem, P.n_max, P.csr_words, P.gstate + (size_t)blockIdx.x * (size_t)P.gstate_bytes);
     w.init_scratch(P.n_max);
