@@ -201,6 +201,14 @@ int vc_mvc_noalloc(const vc_graph *g, const vc_config *cfg, void *stream, int32_
  * error code. */
 int vc_last_sm_nodes(int64_t *counts_out, int32_t capacity);
 
+/* Measurement helper (no counterpart in the paper): copies `bytes` from src to dst `passes` times in
+ * one launch on `stream`, with every load and store through L2 only.  With a working set well
+ * below the L2 size (for example 2 x 16 MiB) the launch time gives the L2 bandwidth that the
+ * traversal's roofline is stated against (2 * bytes * passes moved).  dst and src are device
+ * pointers, 16-byte aligned, bytes a multiple of 16, passes >= 1; VC_EINVAL otherwise.  Does not
+ * wait for the stream. */
+int vc_l2_copy_probe(void *dst, const void *src, size_t bytes, int32_t passes, void *stream);
+
 /* Releases the cached device scratch of the current device. */
 int vc_release(void);
 /* Short name of a status code. */

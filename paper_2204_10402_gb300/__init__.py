@@ -30,7 +30,7 @@ EXPORTED = ["vc_mvc", "vc_pvc", "vc_mvc_batch", "vc_greedy", "vc_reduce_node", "
             "vc_release", "vc_strerror", "vc_version", "vc_mvc_noalloc",
             "vc_server_create", "vc_server_submit", "vc_server_poll", "vc_server_drain", "vc_server_stats",
             "vc_server_destroy", "vc_plan_create_mvc_batch", "vc_plan_launch", "vc_plan_results",
-            "vc_plan_destroy"]
+            "vc_plan_destroy", "vc_l2_copy_probe"]
 NOALLOC_MAX_N = 512
 
 
@@ -129,6 +129,7 @@ def load(path: str | None = None):
     lib.vc_plan_launch.argtypes = [P, P]
     lib.vc_plan_results.argtypes = [P, P, P, P, i32, sp]
     lib.vc_plan_destroy.argtypes = [P]
+    lib.vc_l2_copy_probe.argtypes = [P, P, ctypes.c_size_t, i32, P]
     lib.vc_release.argtypes = []
     lib.vc_strerror.argtypes = [ctypes.c_int]
     lib.vc_strerror.restype = ctypes.c_char_p
@@ -357,6 +358,14 @@ def last_sm_nodes() -> np.ndarray:
     if rc < 0:
         raise VCError(rc, "vc_last_sm_nodes")
     return buf[:rc].copy()
+
+
+def l2_copy_probe(dst, src, passes: int, stream=None):
+    """Copies CUDA tensor src onto dst `passes` times in one launch through L2 (measurement
+    helper; see vc_l2_copy_probe).  Returns without waiting for the stream."""
+    assert _is_cuda_tensor(dst) and _is_cuda_tensor(src) and dst.numel() * dst.element_size() == src.numel() * src.element_size()
+    _check(load().vc_l2_copy_probe(dst.data_ptr(), src.data_ptr(), src.numel() * src.element_size(), int(passes),
+                                   _stream(stream)), "vc_l2_copy_probe")
 
 
 def release():

@@ -429,3 +429,18 @@ def test_per_sm_load_counts(vc):
     per_sm = vc.last_sm_nodes()
     assert per_sm.sum() == st["nodes_visited"]
     assert (per_sm > 0).sum() >= 100
+
+
+def test_l2_copy_probe(vc):
+    # The roofline's L2 probe: after p passes dst holds src with the pass index p-1 folded into
+    # the first word of every 16 bytes.
+    import torch
+    src = torch.arange(1 << 16, dtype=torch.int32, device="cuda")
+    dst = torch.zeros_like(src)
+    vc.l2_copy_probe(dst, src, 3)
+    torch.cuda.synchronize()
+    want = src.clone().view(-1, 4)
+    want[:, 0] ^= 2
+    assert torch.equal(dst.view(-1, 4), want)
+    with pytest.raises(vc.VCError):
+        vc.l2_copy_probe(dst[1:], src[1:], 1)  # not 16-byte aligned
