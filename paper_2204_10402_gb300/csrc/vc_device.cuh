@@ -40,6 +40,7 @@ enum : int {
     kScB4 = 6,
     kScB5 = 7,
     kScWlHint = 40, // worklist fill seen by the node's snapshot
+    kScMaxDeg = 41, // bit-row workers: an upper bound on the current node's largest live degree
     kScKeys = 48,   // 16 x u64 per-warp argmax keys (words 48..79)
 };
 
@@ -554,16 +555,22 @@ struct Worker {
     __device__ __forceinline__ bool row_has(int u, int x) const { return (rows[u * NW + (x >> 5)] >> (x & 31)) & 1u; }
 
     // Live mask of the current node from its degree array (after a node is loaded).
+    // (Also the bound on the largest live degree that lets high-degree passes be skipped.)
     __device__ void init_live(const Ctx &c) {
+        int mx = 0;
 #pragma unroll 1
         for (int k = 0; k < NW; ++k) {
             const int v = 32 * k + lane;
-            const unsigned m = __ballot_sync(kFull, v < c.n && deg(v) != -1);
+            const int dv = v < c.n ? deg(v) : -1;
+            const unsigned m = __ballot_sync(kFull, dv != -1);
+            mx = max(mx, dv);
             if (lane == 0) {
                 livew[k] = m;
                 newm[k] = 0u;
             }
         }
+        mx = (int)__reduce_max_sync(kFull, (unsigned)max(mx, 0));
+        if (lane == 0) sc[kScMaxDeg] = mx;
         __syncwarp();
     }
 
@@ -706,7 +713,7 @@ struct Worker {
                 tally[kTCsr] += (unsigned long long)(c.off[u + 1] - c.off[u]);
             }
         } else {
-            int degsum = 0, words = 0;
+            int degsum = 0, words = 0, maxd = 0;
 #pragma unroll 1
             for (int k = 0; k < chunks; ++k) {
                 const int v = 32 * k + lane;
@@ -727,6 +734,7 @@ struct Worker {
                             changed = true;
                         }
                         degsum += nd;
+                        maxd = max(maxd, nd);
                     }
                 }
                 const unsigned chg = __ballot_sync(kFull, changed);
@@ -734,9 +742,11 @@ struct Worker {
             }
             degsum = __reduce_add_sync(kFull, degsum);
             words = __reduce_add_sync(kFull, words);
+            const int mx = (int)__reduce_max_sync(kFull, (unsigned)maxd);
             if (lane == 0) {
                 hdr->S += cnt;
                 hdr->m = degsum / 2;
+                sc[kScMaxDeg] = mx;
                 tally[kTCsr] += (unsigned long long)words;
             }
         }
@@ -824,9 +834,12 @@ struct Worker {
     }
 
     // High-degree over the lanes' own vertices: one ballot per 32 vertices.
+    // Skipped (finds nothing, scans nothing) while the largest live degree cannot exceed the
+    // threshold: degrees only fall within a node, so the bound from the last recount holds.
     __device__ bool rows_pass_high_degree(const Ctx &c, int32_t bound) {
         const long long t0 = VC_CYC();
         const int thr = (c.kind == kMVC) ? bound - hdr->S - 1 : bound - hdr->S;
+        if (sc[kScMaxDeg] <= thr) return false;
         bool proposed = false;
         const int chunks = (c.n + 31) >> 5;
 #pragma unroll
