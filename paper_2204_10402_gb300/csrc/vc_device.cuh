@@ -40,7 +40,8 @@ enum : int {
     kScB4 = 6,
     kScB5 = 7,
     kScWlHint = 40, // worklist fill seen by the node's snapshot
-    kScMaxDeg = 41, // bit-row workers: an upper bound on the current node's largest live degree
+    kScMaxDeg = 41, // an upper bound on the current node's largest live degree (degrees only fall)
+    kScMaxDegNext = 42, // CSR-walk workers: the bound a running high-degree pass collects
     kScKeys = 48,   // 16 x u64 per-warp argmax keys (words 48..79)
 };
 
@@ -448,7 +449,7 @@ struct Worker {
             if constexpr (NW == 0) marks[i] = 0;  // bit-row workers have no marks
             dirty[i] = 0ull;
         }
-        for (int i = tid; i < kScratchWords; i += WT) sc[i] = 0;
+        for (int i = tid; i < kScratchWords; i += WT) sc[i] = (i == kScMaxDeg) ? INT32_MAX : 0;
         if constexpr (NW > 0)
             for (int i = tid; i < 2 * kMaskWords; i += WT) livew[i] = 0u;  // live and chosen masks
         sync();
@@ -582,6 +583,7 @@ struct Worker {
         sync();  // no warp still reads the node being replaced
         for (int v = tid; v < c.n; v += WT) d[v] = (W)(c.off[v + 1] - c.off[v]);
         dirty_all(c.n);
+        if (tid == 0) sc[kScMaxDeg] = INT32_MAX;  // unknown until a high-degree pass or a recount
         if (tid == 0) {
             hdr->problem = c.index;
             hdr->S = 0;
@@ -609,6 +611,7 @@ struct Worker {
             for (int i = tid; i < bytes / 16; i += WT) t[i] = __ldcg(s + i);
         }
         dirty_none(n_max);
+        if (tid == 0) sc[kScMaxDeg] = INT32_MAX;
         sync();
     }
 
@@ -1028,19 +1031,33 @@ struct Worker {
     // for MVC, k-|S| for PVC (`bound` is best or k).  (Computing argmax keys in this scan, to
     // spare argmax() its own scan after the last pass, measured 5 % slower: every pass paid for
     // keys only the last one needs.)
+    // Skipped while the bound on the largest live degree is at most the threshold.  A pass that
+    // runs leaves as the new bound the largest degree it did not choose (the chosen vertices
+    // leave the graph and the rest only lose degree).
     __device__ bool pass_high_degree(const Ctx &c, int32_t bound) {
         if constexpr (NW > 0) return rows_pass_high_degree(c, bound);
         const long long t0 = VC_CYC();
         const int thr = (c.kind == kMVC) ? bound - hdr->S - 1 : bound - hdr->S;
+        if (sc[kScMaxDeg] <= thr) return false;
         bool proposed = false;
+        int mx = 0;
         for (int v = tid; v < c.n; v += WT) {
             const int dv = deg(v);
             if (dv != -1 && dv > thr) {
                 propose(v);
                 proposed = true;
+            } else if (dv > mx) {
+                mx = dv;
             }
         }
-        return finish_pass(proposed, kPHigh, t0);
+        mx = (int)__reduce_max_sync(kFull, (unsigned)mx);
+        if (lane == 0 && mx > 0) atomicMax(&sc[kScMaxDegNext], mx);
+        const bool any = finish_pass(proposed, kPHigh, t0);  // ends with a barrier
+        if (tid == 0) {  // read by the next high-degree pass, after further barriers
+            sc[kScMaxDeg] = sc[kScMaxDegNext];
+            sc[kScMaxDegNext] = 0;
+        }
+        return any;
     }
 
     // |S| part of the stop check: MVC needs |S| < best, PVC needs |S| <= k.
