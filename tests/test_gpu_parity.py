@@ -444,3 +444,30 @@ def test_l2_copy_probe(vc):
     assert torch.equal(dst.view(-1, 4), want)
     with pytest.raises(vc.VCError):
         vc.l2_copy_probe(dst[1:], src[1:], 1)  # not 16-byte aligned
+
+
+def boundary_graphs():
+    """Graphs at the bit-row word boundaries (32, 64, 128, 256 vertices and one either side), with
+    closed-form answers or small enough for the oracle."""
+    cases = [(G.complete(n), n - 1) for n in (31, 32, 33)]
+    cases += [(G.path(n), n // 2) for n in (63, 64, 65)] + [(G.cycle(n), (n + 1) // 2) for n in (127, 128, 129)]
+    cases += [(G.star(n - 1), 1) for n in (255, 256)] + [(G.complete_bipartite(16, 48), 16)]
+    for n, p in ((1, 0.5), (2, 1.0), (3, 0.7), (31, 0.2), (33, 0.3), (63, 0.1), (65, 0.12), (127, 0.05),
+                 (128, 0.06), (129, 0.04), (200, 0.02), (256, 0.015)):
+        g = G.gnp(n, p, 7000 + n)
+        cases.append((g, None))
+    return cases
+
+
+@pytest.mark.parametrize("bit_rows", [1, -1])
+def test_bit_row_size_boundaries(vc, bit_rows):
+    for g, want in boundary_graphs():
+        if want is None:
+            want, _, _ = oracle.mvc(g)
+        a = vc.mvc(g.offsets, g.neighbors, config=vc.make_config(bit_rows=bit_rows))
+        assert a.value == want, (g.n, g.m)
+        words = 0 if bit_rows < 0 else (1 if g.n <= 32 else 2 if g.n <= 64 else 4 if g.n <= 128 else 8)
+        assert a.stats["bit_rows"] == words, g.n
+        check_cover(g, a.cover, want)
+        p = vc.pvc(g.offsets, g.neighbors, want - 1, config=vc.make_config(bit_rows=bit_rows))
+        assert p.value == 0  # no cover below the minimum (and k = -1 is always no)
