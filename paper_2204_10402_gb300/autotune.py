@@ -29,7 +29,7 @@ SPACE = {
     "worker_threads": (32, 64, 128, 256),
     "width": (16, 32),
     "donate_threshold": (0.25, 0.5, 1.0),
-    "worklist_capacity": (16384, 65536, 262144),
+    "worklist_capacity": (65536, 262144, 524288),
     "stage_csr": (0, 1, -1),
     "node_in_global": (0, 1),
     "bit_rows": (0, 1, -1),

@@ -170,7 +170,8 @@ VC_HD inline int32_t smem_bytes_for(int32_t n_max, int32_t width_bytes, int32_t 
 // (paper_2204_10402_gb300/autotune.py; coordinate descent over worker size, width, threshold,
 // capacity and staging):
 //   n <= 64    4096 G(n,p), n 20-64           one warp, 32-bit entries, threshold 0.25
-//   n <= 128   4096 G(n,p), n 20-120          one warp, 16-bit entries, threshold 0.5
+//   n <= 128   4096 G(n,p), n 20-120          one warp, 32-bit entries, threshold 0.5 (with bit
+//                                             rows; 16-bit entries were best for CSR walks)
 //   n <= 400   planted-clique G(160/200, .05) one warp, 32-bit entries (1935 -> 1400 ms at n = 200)
 //   n <= 1200  two warps; n <= 2560 four warps; larger: eight warps, threshold 0.25
 struct LaunchDefaults {
@@ -180,18 +181,19 @@ struct LaunchDefaults {
 };
 VC_HD inline LaunchDefaults tuned_defaults(int32_t n_max) {
     if (n_max <= 64) return {32, 32, 0.25f};
-    if (n_max <= 128) return {32, 16, 0.5f};
+    if (n_max <= 128) return {32, 32, 0.5f};
     if (n_max <= 400) return {32, 32, 0.5f};
     if (n_max <= 1200) return {64, 16, 0.5f};
     if (n_max <= 2560) return {128, 16, 0.5f};
     return {256, n_max <= 32768 ? 16 : 32, 0.25f};
 }
 
-// Default worklist capacity: the largest power of two up to 262144 entries whose slots fit in
-// 1 GiB (Sec. V-A tries 128K-512K entries; measured on the 4096-graph batch: 16K entries 388 ms,
-// 64K 348 ms, 256K 290 ms per launch).
+// Default worklist capacity: the largest power of two up to 524288 entries whose slots fit in
+// 1 GiB (Sec. V-A tries 128K-512K entries).  Measured on the 4096-graph batch: CSR walks 16K
+// entries 388 ms, 64K 348 ms, 256K 290 ms per launch; bit rows 64K 238 ms, 128K 197 ms, 256K
+// 169 ms, 512K 167 ms, 1M 167 ms.
 VC_HD inline int32_t default_worklist_capacity(int32_t entry_bytes) {
-    int64_t cap = 262144;
+    int64_t cap = 524288;
     while (cap > 1024 && cap * (int64_t)entry_bytes > (int64_t(1) << 30)) cap >>= 1;
     return (int32_t)cap;
 }
