@@ -214,7 +214,9 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        # raw samples go to $VC_CLOCKS_DIR (default: the system temp dir); the JSON line summarises them
+        import tempfile
+        self.path = os.path.join(os.environ.get("VC_CLOCKS_DIR", tempfile.gettempdir()), f"vc_clocks_gpu{gpu_index}.csv")
 
     def __enter__(self):
         try:
