@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "vc_internal.h"
+#include "vc_tuning.h"
 #include "vc_launch.h"
 
 namespace vc {
@@ -228,7 +229,7 @@ int run(Workspace &ws, const Spec &spec, const vc_config *cfg_in, cudaStream_t s
     const int32_t eb = entry_bytes_for(n_max, wbytes);
 
     // ---- worklist sizing (Sec. V-A explores 128K-512K entries, threshold 0.25-1.0 x size) ----
-    int cap = cfg.worklist_capacity > 0 ? next_pow2(cfg.worklist_capacity) : default_worklist_capacity(eb);
+    int cap = cfg.worklist_capacity > 0 ? next_pow2(cfg.worklist_capacity) : default_worklist_capacity(eb, tuned.capacity);
     float frac = cfg.donate_threshold > 0.f ? cfg.donate_threshold : tuned.threshold;
     int threshold = (int)std::max<double>(0.0, std::min<double>(cap, (double)frac * cap));
     if (cfg.donate_threshold < 0.f) threshold = 0;  // never donate (stress setting)

@@ -166,50 +166,11 @@ VC_HD inline int32_t smem_bytes_for(int32_t n_max, int32_t width_bytes, int32_t 
     return (int32_t)b;
 }
 
-// Built-in launch defaults per graph-size class, from autotuner runs on a GB300
-// (paper_2204_10402_gb300/autotune.py; coordinate descent over worker size, width, threshold,
-// capacity and staging):
-//   n <= 64    4096 G(n,p), n 20-64           one warp, 32-bit entries, threshold 0.25
-//   n <= 128   4096 G(n,p), n 20-120          one warp, 32-bit entries, threshold 0.5 (with bit
-//                                             rows; 16-bit entries were best for CSR walks)
-//   n <= 400   planted-clique G(160/200, .05) one warp, 32-bit entries (1935 -> 1400 ms at n = 200)
-//   n <= 1200  two warps; n <= 2560 four warps; larger: eight warps, threshold 0.25
-struct LaunchDefaults {
-    int32_t worker_threads;
-    int32_t width;
-    float threshold;
-};
-VC_HD inline LaunchDefaults tuned_defaults(int32_t n_max) {
-    if (n_max <= 64) return {32, 32, 0.25f};
-    if (n_max <= 128) return {32, 32, 0.5f};
-    if (n_max <= 400) return {32, 32, 0.5f};
-    if (n_max <= 1200) return {64, 16, 0.5f};
-    if (n_max <= 2560) return {128, 16, 0.5f};
-    return {256, n_max <= 32768 ? 16 : 32, 0.25f};
-}
-
-// Default worklist capacity: the largest power of two up to 524288 entries whose slots fit in
-// 1 GiB (Sec. V-A tries 128K-512K entries).  Measured on the 4096-graph batch: CSR walks 16K
-// entries 388 ms, 64K 348 ms, 256K 290 ms per launch; bit rows 64K 238 ms, 128K 197 ms, 256K
-// 169 ms, 512K 167 ms, 1M 167 ms.
-VC_HD inline int32_t default_worklist_capacity(int32_t entry_bytes) {
-    int64_t cap = 524288;
-    while (cap > 1024 && cap * (int64_t)entry_bytes > (int64_t(1) << 30)) cap >>= 1;
-    return (int32_t)cap;
-}
-
 // Global-state variant (Sec. IV-E: the paper's kernel version that keeps the current intermediate
 // graph in global memory): shared memory keeps only the 16-byte header, the scratch words and any
 // staged CSR; the degree array, marks, dirty bits and removal list live in a per-worker region.
 VC_HD inline int32_t smem_bytes_gm(int32_t csr_words) {
     return 16 + kScratchWords * 4 + pad16((int64_t)csr_words * 4);
-}
-// Bit-row workers: words per adjacency row for graphs of at most n_max vertices (0 = none).
-// By default only up to 4 words: on the planted-clique graphs (n = 160-200, p = 0.05) 8-word rows
-// ran 1.5-2.3x slower than CSR walks (sparse rows, and fewer workers fit), so they are used only
-// on request (`forced`).
-VC_HD inline int32_t rows_words_for(int32_t n_max, bool forced = false) {
-    return n_max <= 32 ? 1 : n_max <= 64 ? 2 : n_max <= 128 ? 4 : (forced && n_max <= 256) ? 8 : 0;
 }
 VC_HD inline int32_t gstate_bytes_for(int32_t n_max, int32_t width_bytes) {
     int64_t b = pad16((int64_t)n_max * width_bytes);
@@ -217,13 +178,6 @@ VC_HD inline int32_t gstate_bytes_for(int32_t n_max, int32_t width_bytes) {
     b += pad16(((int64_t)n_max + 31) / 32 * 8);
     b += pad16((int64_t)n_max * 4);
     return (int32_t)b;
-}
-
-// Shared-memory CSR staging by default: the offsets (n+1 ints) of graphs with up to
-// kOffsetStageN vertices; nothing for larger graphs (their workers share the CSR through L1).
-constexpr int32_t kOffsetStageN = 1024;
-VC_HD inline int32_t default_csr_words(int32_t n_max, int32_t stage_csr) {
-    return (stage_csr == 0 && n_max <= kOffsetStageN) ? n_max + 1 : 0;
 }
 
 }  // namespace vc

@@ -21,6 +21,7 @@
 #include <mutex>
 
 #include "vc_internal.h"
+#include "vc_tuning.h"
 #include "vc_launch.h"
 
 namespace vc {

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "vc_internal.h"
+#include "vc_tuning.h"
 #include "vc_launch.h"
 #include "../../include/vc_plan.h"
 
@@ -116,7 +117,7 @@ int vc_plan_create_mvc_batch(int32_t G, const int32_t *vtx, const int32_t *edge,
     if (cfg.worklist_capacity > 0)
         while (cap < cfg.worklist_capacity) cap <<= 1;
     else
-        cap = default_worklist_capacity(pl->eb);
+        cap = default_worklist_capacity(pl->eb, tuned.capacity);
     pl->cap = cap;
     const float frac = cfg.donate_threshold > 0.f ? cfg.donate_threshold : tuned.threshold;
     const int threshold = cfg.donate_threshold < 0.f ? 0 : std::max(0, std::min(cap, (int)(frac * cap)));

@@ -29,6 +29,7 @@
 #include <vector>
 
 #include "vc_internal.h"
+#include "vc_tuning.h"
 #include "vc_launch.h"
 #include "../../include/vc_server.h"
 
