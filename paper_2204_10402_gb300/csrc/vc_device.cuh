@@ -211,6 +211,7 @@ static_assert(kScProf + 2 * kProfSlots <= kScratchWords, "profile slots exceed t
 #define VC_CYC() 0ll
 #define VC_CYC_ADD(w, slot, t0) \
     do {                        \
+        (void)(t0);             \
     } while (0)
 #define VC_CYC_INC(w, slot) \
     do {                    \
@@ -227,6 +228,7 @@ static_assert(kScProf + 2 * kProfSlots <= kScratchWords, "profile slots exceed t
 #define VC_TRACE_NOW() 0ull
 #define VC_TRACE_ADD(w, slot, t0) \
     do {                          \
+        (void)(t0);               \
     } while (0)
 #endif
 
@@ -504,22 +506,22 @@ struct Worker {
             }
             const V *g = reinterpret_cast<const V *>(grows);
             for (int v = lane; v < c.n; v += 32) r[v] = RowVec<kNW>::load_cg(g + v);
-            return;
-        }
-        for (int v = lane; v < c.n; v += 32) {
-            uint32_t b[kNW];
+        } else {
+            for (int v = lane; v < c.n; v += 32) {
+                uint32_t b[kNW];
 #pragma unroll
-            for (int w = 0; w < NW; ++w) b[w] = 0u;
-            const int lo = c.off[v], hi = c.off[v + 1];
-            for (int j = lo; j < hi; ++j) {
-                const int x = c.adj[j];
-                VC_CHECK(dbg, x >= 0 && x < 32 * NW, 21, x, continue);
+                for (int w = 0; w < NW; ++w) b[w] = 0u;
+                const int lo = c.off[v], hi = c.off[v + 1];
+                for (int j = lo; j < hi; ++j) {
+                    const int x = c.adj[j];
+                    VC_CHECK(dbg, x >= 0 && x < 32 * NW, 21, x, continue);
 #pragma unroll
-                for (int w = 0; w < NW; ++w) b[w] |= ((x >> 5) == w) ? (1u << (x & 31)) : 0u;
+                    for (int w = 0; w < NW; ++w) b[w] |= ((x >> 5) == w) ? (1u << (x & 31)) : 0u;
+                }
+                const V q = RowVec<kNW>::pack(b);
+                r[v] = q;
+                if (grows) RowVec<kNW>::store_cg(reinterpret_cast<V *>(grows) + v, q);
             }
-            const V q = RowVec<kNW>::pack(b);
-            r[v] = q;
-            if (grows) RowVec<kNW>::store_cg(reinterpret_cast<V *>(grows) + v, q);
         }
     }
 
