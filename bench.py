@@ -94,16 +94,17 @@ TRAVERSAL_SOURCES = ("vc_internal.h", "vc_device.cuh", "vc_kernels.cuh", "vc_lau
                      "vc_kern_w16_rows.cu", "vc_kern_w32_rows.cu")
 
 
-def measured_traffic_per_node():
-    """DRAM bytes per tree node of the traversal kernel from the committed ncu summary, or None
-    when the kernel sources changed since that capture (the summary records their hash)."""
+def measured_per_node(key: str = "dram_bytes_per_tree_node"):
+    """A per-tree-node figure of the traversal kernel (DRAM bytes, warp instructions) from the
+    committed ncu summary, or None when the kernel sources changed since that capture (the
+    summary records their hash)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "traverse_kernel_batch_gnp.md")
     if not os.path.exists(path):
         return None
     rec = {}
     for line in open(path):
-        if ":" in line and line.split(":")[0] in ("kernel_source_hash", "dram_bytes_per_tree_node"):
+        if ":" in line and line.split(":")[0] in ("kernel_source_hash", key):
             k, v = line.split(":", 1)
             rec[k] = v.strip()
     csrc = os.path.join(ROOT, "paper_2204_10402_gb300", "csrc")
@@ -112,9 +113,9 @@ def measured_traffic_per_node():
         h.update(f.encode())
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
-    if rec.get("kernel_source_hash") != h.hexdigest()[:16] or "dram_bytes_per_tree_node" not in rec:
+    if rec.get("kernel_source_hash") != h.hexdigest()[:16] or key not in rec:
         return None
-    return float(rec["dram_bytes_per_tree_node"])
+    return float(rec[key])
 
 
 def l2_copy_peak(vc, dev) -> float:
@@ -351,7 +352,8 @@ def run_ours(a):
         alg_bytes = [s["entry_bytes_moved"] + 4 * s["csr_words"] for s in stats]
         ach = [bb / (km * 1e-3) / 1e9 for bb, km in zip(alg_bytes, kernel_ms) if km > 0]
         achieved = statistics.mean(ach) if ach else 0.0
-        per_node = measured_traffic_per_node()
+        per_node = measured_per_node("dram_bytes_per_tree_node")
+        inst_per_node = measured_per_node("warp_instructions_per_tree_node")
         nodes_per_launch = statistics.mean(s["nodes_visited"] for s in stats)
         l2_peak = l2_copy_peak(vc, dev)
         roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
@@ -363,6 +365,18 @@ def run_ours(a):
                     "alg_bytes_per_launch": statistics.mean(alg_bytes),
                     "l2": {"peak_probe_gbs": l2_peak, "frac": achieved / l2_peak,
                            "probe": "vc_l2_copy_probe: 16 MiB onto 16 MiB x 64 passes in one launch, .cg loads/stores, read+write bytes"}}
+        if inst_per_node is not None:
+            # What actually bounds the traversal: warp-instruction issue.  Instructions per node
+            # from the ncu capture x nodes of this launch / its event time, against one warp
+            # instruction per scheduler per cycle (4 per SM) at the SM clock sampled in the run.
+            sms = torch.cuda.get_device_properties(dev).multi_processor_count
+            mhz = clk.summary().get("sm_mhz") or 0.0
+            ginst = inst_per_node * nodes_per_launch / (statistics.mean(kernel_ms) * 1e-3) / 1e9
+            peak_ginst = sms * 4 * mhz / 1e3
+            roofline["issue"] = {"achieved": ginst, "peak": peak_ginst, "unit": "G warp-inst/s",
+                                 "frac": ginst / peak_ginst if peak_ginst else None,
+                                 "note": "ncu warp instructions per tree node x nodes / kernel time; "
+                                         "peak = SMs x 4 schedulers x sampled SM clock"}
         line = {
             "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": 1000 * t_max / a.steps, "higher_is_better": True,
