@@ -46,3 +46,35 @@ def test_host_only_calls(lib):
     lib.vc_strerror.restype = ctypes.c_char_p
     assert lib.vc_strerror(-1) == b"VC_EINVAL"
     assert lib.vc_strerror(0) == b"VC_OK"
+
+
+def _c_layout(tmp_path, type_name, fields, header):
+    """sizeof and field offsets of a C struct, from a tiny C program compiled with the host gcc."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    lines = [f'#include "{header}"', "#include <stddef.h>", "#include <stdio.h>", "int main(void) {",
+             f'  printf("%zu\\n", sizeof({type_name}));']
+    lines += [f'  printf("%zu\\n", offsetof({type_name}, {f}));' for f in fields]
+    lines += ["  return 0;", "}"]
+    src = tmp_path / f"{type_name}.c"
+    exe = tmp_path / f"{type_name}.out"
+    src.write_text("\n".join(lines))
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
+    return int(out[0]), [int(x) for x in out[1:]]
+
+
+@pytest.mark.parametrize("type_name,header,cls", [
+    ("vc_graph", "vc.h", "Graph"), ("vc_config", "vc.h", "Config"), ("vc_stats", "vc.h", "Stats"),
+    ("vc_request_info", "vc_server.h", "RequestInfo"), ("vc_server_counters", "vc_server.h", "ServerCounters")])
+def test_struct_layouts_match_binding(tmp_path, type_name, header, cls):
+    # The ctypes mirrors must have the C structs' sizes and field offsets exactly.
+    import paper_2204_10402_gb300 as vc
+    py = getattr(vc, cls)
+    fields = [name for name, _ in py._fields_]
+    size, offsets = _c_layout(tmp_path, type_name, fields, header)
+    assert ctypes.sizeof(py) == size
+    assert [getattr(py, f).offset for f in fields] == offsets
