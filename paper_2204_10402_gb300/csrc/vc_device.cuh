@@ -544,17 +544,6 @@ struct Worker {
             if (b[w]) u = 32 * w + __ffs(b[w]) - 1;
         return u;
     }
-    // Clears the lowest set bit over NW words.
-    static __device__ __forceinline__ void clear_first(uint32_t (&b)[kNW]) {
-        bool done = false;
-#pragma unroll
-        for (int w = 0; w < NW; ++w) {
-            if (!done && b[w]) {
-                b[w] &= b[w] - 1u;
-                done = true;
-            }
-        }
-    }
     __device__ __forceinline__ bool row_has(int u, int x) const { return (rows[u * NW + (x >> 5)] >> (x & 31)) & 1u; }
 
     // Live mask of the current node from its degree array (after a node is loaded).
@@ -825,10 +814,16 @@ struct Worker {
                 live_words(lv);
 #pragma unroll
                 for (int w = 0; w < NW; ++w) b[w] &= lv[w];
-                const int u = first_bit(b);
-                clear_first(b);
-                const int x = first_bit(b);
-                if (u >= 0 && x >= 0 && row_has(u, x) && !((deg(u) == 2 && u < v) || (deg(x) == 2 && x < v))) {
+                // deg(v) = 2: exactly two bits are set; u is the lowest, x the highest
+                int u = -1, x = -1;
+#pragma unroll
+                for (int w = 0; w < NW; ++w) {
+                    if (b[w]) {
+                        if (u < 0) u = 32 * w + __ffs(b[w]) - 1;
+                        x = 32 * w + 31 - __clz(b[w]);
+                    }
+                }
+                if (u >= 0 && x > u && row_has(u, x) && !((deg(u) == 2 && u < v) || (deg(x) == 2 && x < v))) {
                     atomicOr(&newm[u >> 5], 1u << (u & 31));
                     atomicOr(&newm[x >> 5], 1u << (x & 31));
                     proposed = true;
