@@ -102,7 +102,8 @@ typedef struct {
     int64_t worklist_pops;      /* worklist entries taken */
     int64_t rule_passes;        /* reduction-rule passes (each scans one degree array) */
     int64_t csr_words;          /* CSR neighbour words read during the search */
-    int64_t entry_bytes_moved;  /* degree-array entry bytes copied between shared and global memory */
+    int64_t entry_bytes_moved;  /* entry bytes copied between shared and global memory: entry size x (pops + pushes +
+                                   donations + worklist pops) */
     int32_t max_depth;          /* deepest local stack seen */
     int32_t greedy_ub;          /* greedy upper bound (single-graph calls; batch: sum over graphs) */
     int32_t workers;            /* persistent workers launched */

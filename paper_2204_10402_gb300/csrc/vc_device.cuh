@@ -160,7 +160,6 @@ enum TallySlot : int {
     kTDequeues,
     kTPasses,
     kTCsr,
-    kTBytes,
     kTMaxDepth,
     kTWaitNs,     // VC_TRACE: time spent waiting for work (worklist, roots, idle)
     kTReduceNs,   // VC_TRACE: reduction rules and stop check
@@ -536,14 +535,6 @@ struct Worker {
     __device__ __forceinline__ void chosen_words(uint32_t (&b)[kNW]) const {
         RowVec<kNW>::unpack(*reinterpret_cast<const typename RowVec<kNW>::type *>(newm), b);
     }
-    // Lowest set bit over NW words, or -1.
-    static __device__ __forceinline__ int first_bit(const uint32_t (&b)[kNW]) {
-        int u = -1;
-#pragma unroll
-        for (int w = NW - 1; w >= 0; --w)
-            if (b[w]) u = 32 * w + __ffs(b[w]) - 1;
-        return u;
-    }
     __device__ __forceinline__ bool row_has(int u, int x) const { return (rows[u * NW + (x >> 5)] >> (x & 31)) & 1u; }
 
     // Live mask of the current node from its degree array (after a node is loaded).
@@ -782,9 +773,13 @@ struct Worker {
                 uint32_t b[kNW], lv[kNW];
                 row(v, b);
                 live_words(lv);
+                // deg(v) = 1: exactly one bit is set
+                int u = -1;
 #pragma unroll
-                for (int w = 0; w < NW; ++w) b[w] &= lv[w];
-                const int u = first_bit(b);
+                for (int w = 0; w < NW; ++w) {
+                    const uint32_t m = b[w] & lv[w];
+                    if (m) u = 32 * w + __ffs(m) - 1;
+                }
                 if (u >= 0 && !(deg(u) == 1 && u > v)) {
                     atomicOr(&newm[u >> 5], 1u << (u & 31));
                     proposed = true;

@@ -150,7 +150,7 @@ struct Result {
     std::vector<Problem> probs;
     Control ctrl;
     float kernel_ms = 0.f;
-    int workers = 0, wt = 0, width = 0, stack_depth = 0, nw = 0;
+    int workers = 0, wt = 0, width = 0, stack_depth = 0, nw = 0, eb = 0;
     bool csr_staged = false, gm = false;
 };
 
@@ -367,6 +367,7 @@ int run(Workspace &ws, const Spec &spec, const vc_config *cfg_in, cudaStream_t s
     res.csr_staged = csr_words > 0;
     res.gm = gm;
     res.nw = nw;
+    res.eb = eb;
     res.stack_depth = spec.search ? (int)depth : 0;
     return h_ctrl->status;
 }
@@ -381,7 +382,9 @@ void fill_stats(vc_stats *st, const Result &r, double total_ms, int32_t greedy) 
     st->worklist_pops = (int64_t)r.ctrl.worklist_pops;
     st->rule_passes = (int64_t)r.ctrl.rule_passes;
     st->csr_words = (int64_t)r.ctrl.csr_words;
-    st->entry_bytes_moved = (int64_t)r.ctrl.entry_bytes;
+    // every pop, push, donation and dequeue copies one entry
+    st->entry_bytes_moved = (int64_t)r.eb * (int64_t)(r.ctrl.stack_pops + r.ctrl.stack_pushes + r.ctrl.donations +
+                                                       r.ctrl.worklist_pops);
     for (int i = 0; i < 4; ++i) st->trace_ns[i] = (int64_t)r.ctrl.trace_ns[i];
     st->idle_polls = (int64_t)r.ctrl.idle_polls;
     for (int i = 0; i < 16; ++i) st->trace_cycles[i] = (int64_t)r.ctrl.trace_cycles[i];

@@ -79,7 +79,6 @@ struct alignas(128) Control {
     unsigned long long worklist_pops;
     unsigned long long rule_passes;
     unsigned long long csr_words;
-    unsigned long long entry_bytes;
     unsigned long long trace_ns[4];  // VC_TRACE builds: ns waiting for work, reducing, branching, solutions
     unsigned long long idle_polls;   // VC_TRACE builds: idle-loop iterations
     unsigned long long trace_cycles[16];  // VC_TRACE builds: SM cycles per activity (ProfSlot)

@@ -360,7 +360,6 @@ __device__ int acquire(const Params &P, Worker<W, WT, GM, NW> &w) {
             st_release_u32(&P.wl_seq[slot], pos + (uint32_t)P.wl_capacity);
             atomicAdd(&ctrl->wl_space, 1);
             w.tally[kTDequeues] += 1;
-            w.tally[kTBytes] += (unsigned long long)P.entry_bytes;
         }
     }
     return result;
@@ -412,7 +411,6 @@ __global__ void __launch_bounds__(kMaxThreads(WT), kMinBlocks(WT)) traverse_kern
             if constexpr (NW > 0) w.init_live(c);
             if (w.tid == 0) {
                 w.tally[kTPops] += 1;
-                w.tally[kTBytes] += (unsigned long long)eb;
             }
             VC_CYC_ADD(w, kPPop, t_pop);
         } else {
@@ -519,7 +517,6 @@ __global__ void __launch_bounds__(kMaxThreads(WT), kMinBlocks(WT)) traverse_kern
                         st_release_u32(&P.wl_seq[pos & wl_mask], pos + 1u);
                         atomicAdd(&ctrl->wl_count, 1);
                         w.tally[kTDonations] += 1;
-                        w.tally[kTBytes] += (unsigned long long)eb;
                     }
                 } else {  // push on the local stack
                     if (top >= P.stack_depth) {
@@ -531,7 +528,6 @@ __global__ void __launch_bounds__(kMaxThreads(WT), kMinBlocks(WT)) traverse_kern
                     ++top;
                     if (w.tid == 0) {
                         w.tally[kTPushes] += 1;
-                        w.tally[kTBytes] += (unsigned long long)eb;
                         if ((unsigned long long)top > w.tally[kTMaxDepth]) w.tally[kTMaxDepth] = top;
                     }
                     w.sync();
@@ -556,7 +552,6 @@ __global__ void __launch_bounds__(kMaxThreads(WT), kMinBlocks(WT)) traverse_kern
         atomicAdd(&ctrl->worklist_pops, T[kTDequeues]);
         atomicAdd(&ctrl->rule_passes, T[kTPasses]);
         atomicAdd(&ctrl->csr_words, T[kTCsr]);
-        atomicAdd(&ctrl->entry_bytes, T[kTBytes]);
 #ifdef VC_TRACE
         atomicAdd(&ctrl->trace_ns[0], T[kTWaitNs]);
         atomicAdd(&ctrl->trace_ns[1], T[kTReduceNs]);

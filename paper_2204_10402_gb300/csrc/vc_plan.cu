@@ -257,7 +257,7 @@ int vc_plan_results(vc_plan *pl, void *stream, int32_t *sizes_out, int32_t *cove
         stats->worklist_pops = (int64_t)c.worklist_pops;
         stats->rule_passes = (int64_t)c.rule_passes;
         stats->csr_words = (int64_t)c.csr_words;
-        stats->entry_bytes_moved = (int64_t)c.entry_bytes;
+        stats->entry_bytes_moved = (int64_t)pl->eb * (int64_t)(c.stack_pops + c.stack_pushes + c.donations + c.worklist_pops);
         for (int i = 0; i < 4; ++i) stats->trace_ns[i] = (int64_t)c.trace_ns[i];
         stats->idle_polls = (int64_t)c.idle_polls;
         for (int i = 0; i < 16; ++i) stats->trace_cycles[i] = (int64_t)c.trace_cycles[i];
