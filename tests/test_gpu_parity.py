@@ -471,3 +471,17 @@ def test_bit_row_size_boundaries(vc, bit_rows):
         check_cover(g, a.cover, want)
         p = vc.pvc(g.offsets, g.neighbors, want - 1, config=vc.make_config(bit_rows=bit_rows))
         assert p.value == 0  # no cover below the minimum (and k = -1 is always no)
+
+
+def test_bit_rows_rejected_where_they_cannot_run(vc):
+    # Bit rows need one-warp workers with the node in shared memory and n <= 256.
+    g = G.gnp(60, 0.1, 0)
+    for cfg in (dict(bit_rows=1, worker_threads=64), dict(bit_rows=1, node_in_global=1)):
+        with pytest.raises(vc.VCError):
+            vc.mvc(g.offsets, g.neighbors, config=vc.make_config(**cfg))
+    big = G.gnp(300, 0.02, 1)
+    with pytest.raises(vc.VCError):
+        vc.mvc(big.offsets, big.neighbors, config=vc.make_config(bit_rows=1, worker_threads=32))
+    # auto mode falls back to CSR walks in the same cases
+    a = vc.mvc(g.offsets, g.neighbors, config=vc.make_config(worker_threads=64))
+    assert a.stats["bit_rows"] == 0 and a.value == oracle.mvc(g)[0]
