@@ -699,8 +699,9 @@ struct Worker {
             }
         } else {
             int degsum = 0, words = 0, maxd = 0;
-#pragma unroll 1
-            for (int k = 0; k < chunks; ++k) {
+#pragma unroll
+            for (int k = 0; k < NW; ++k) {
+                if (k >= chunks) break;
                 const int v = 32 * k + lane;
                 bool changed = false;
                 if (v < c.n) {
