@@ -4,16 +4,18 @@
 //
 // Shared-memory layout of a worker (all offsets 16-byte aligned):
 //   [entry]  EntryHeader (16 B) + degree array W[n_max] padded to 16 B   <- copied to/from stacks
-//   [marks]  one bit per vertex: chosen for S in the current pass
+//   [marks]  CSR-walk workers: one bit per vertex, chosen for S in the current pass
 //   [dirty]  one 64-bit word per 32 vertices: low half = degree changed since the degree-one pass
 //            last looked at the vertex, high half = the same for the degree-two-triangle pass
-//   [list]   int32[n_max]: the vertices chosen in the current pass (each once)
-//   [sc]     kScratchWords int32: pass counters, broadcasts, per-warp reduction keys
+//   [list]   CSR-walk workers: int32[n_max], the vertices chosen in the current pass (each once)
+//   [sc]     kScratchWords int32: tallies, broadcasts, per-warp reduction keys, trace slots
 //   [csr]    optional copy of the current graph's CSR (offsets, then neighbours), so that the
 //            adjacency walks of the rules and branches cost shared-memory latency
-//   [rows]   bit-row workers (NW > 0) only: the live-vertex mask and the pass's chosen set (NW
-//            words each, 16 B apart), then the current graph's adjacency as one NW-word bit row
+//   [rows]   bit-row workers (NW > 0) only: the live-vertex mask and the pass's chosen set
+//            (max(NW, 4) words each), then the current graph's adjacency as one NW-word bit row
 //            per vertex (a read-only copy of the CSR, like [csr])
+// The global-memory version (GM) keeps [entry]'s degree array, [marks], [dirty] and [list] in a
+// per-worker global region instead; the header and [sc] stay in shared memory.
 //
 // Degree-array semantics (Sec. IV-B): d[v] >= 0 is v's degree in G - S, d[v] = -1 means v is in S.
 // W is int16_t or int32_t; -1 is the sentinel at both widths.
@@ -151,7 +153,7 @@ __device__ __forceinline__ Ctx make_ctx(const Params &P, int32_t p) {
     return c;
 }
 
-// Per-worker statistics, kept in shared memory (sc words 8..27) so they cost no registers.
+// Per-worker statistics, kept in shared memory (sc words 8..39) so they cost no registers.
 enum TallySlot : int {
     kTNodes = 0,
     kTPushes,
