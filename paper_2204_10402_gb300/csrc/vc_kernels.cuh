@@ -1,4 +1,5 @@
-// vc_kernels.cuh - kernels of libvc (templated on degree-array width W and worker size WT).
+// vc_kernels.cuh - kernels of libvc, templated on the degree-array width W, the worker size WT,
+// the node placement GM (shared or global memory) and the bit-row words NW (0: CSR walks).
 //
 //   validate_kernel     checks the CSR rules of vc.h (one thread per vertex)
 //   greedy_kernel       greedy upper bound per problem (Sec. II-B): seeds best, the cover and the
@@ -285,7 +286,8 @@ __device__ __forceinline__ int serve_wait(const Params &P, int &arg) {
 
 // Finds the next node for a worker whose local stack is empty: an unclaimed root first, then the
 // worklist; idles with a growing sleep while other workers still hold work.  Returns 0 (stop),
-// 1 (a root is loaded) or 2 (a worklist entry is loaded).  Sec. IV-C: the search is over when
+// 1 (a root is loaded), 2 (a worklist entry is loaded) or, in serving launches, 3 (a new request
+// is claimed; see serve_wait).  Sec. IV-C: the search is over when
 // the worklist is empty and no worker holds work, i.e. when no work unit is left.
 template <bool SERVE, typename W, int WT, bool GM, int NW>
 __device__ int acquire(const Params &P, Worker<W, WT, GM, NW> &w) {
