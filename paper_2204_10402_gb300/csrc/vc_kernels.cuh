@@ -462,6 +462,9 @@ __global__ void __launch_bounds__(kMaxThreads(WT), kMinBlocks(WT)) traverse_kern
             if (w.tid == 0) {
                 const unsigned long long nn = ++w.tally[kTNodes];
                 if ((nn & 31) == 0) atomicAdd(&ctrl->heartbeat, 1u);
+                // A busy worker also honours the caller's cancel flag (every 1024 nodes: the flag
+                // may live in host memory); the status read just below then stops it.
+                if ((nn & 1023) == 0 && P.cancel && *P.cancel) raise_status(ctrl, VC_ECANCELLED);
                 if (fresh || (nn & (kSnapshotEvery - 1)) == 0) {
                     w.sc[kScB0] = (c.kind == kMVC) ? ld_relaxed(&c.prob->best) : c.k;
                     w.sc[kScB1] = (c.kind == kPVC) ? ld_relaxed(&c.prob->found) : 0;

@@ -485,3 +485,33 @@ def test_bit_rows_rejected_where_they_cannot_run(vc):
     # auto mode falls back to CSR walks in the same cases
     a = vc.mvc(g.offsets, g.neighbors, config=vc.make_config(worker_threads=64))
     assert a.stats["bit_rows"] == 0 and a.value == oracle.mvc(g)[0]
+
+
+def test_cancel_flag_stops_a_running_search(vc):
+    # The caller's cancel flag (device or host memory) ends even a search whose workers never go
+    # idle; the library answers normally afterwards.
+    import threading
+    import time
+
+    import torch
+    c, m, want = load_clique_golden()[200]
+    g, _ = G.gnp_with_planted_clique(200, 0.05, c, 0)
+    t0 = time.time()
+    full = vc.mvc(g.offsets, g.neighbors, want_cover=False)
+    full_s = time.time() - t0
+    assert full.value == want
+    flag = torch.ones(1, dtype=torch.int32, device="cuda")  # raised before the call
+    with pytest.raises(vc.VCError) as e:
+        vc.mvc(g.offsets, g.neighbors, config=vc.make_config(cancel=flag.data_ptr()))
+    assert e.value.code == -6  # VC_ECANCELLED
+    host_flag = torch.zeros(1, dtype=torch.int32).pin_memory()  # raised by the host mid-search
+    timer = threading.Timer(0.05, lambda: host_flag.fill_(1))
+    t0 = time.time()
+    timer.start()
+    with pytest.raises(vc.VCError) as e:
+        vc.mvc(g.offsets, g.neighbors, config=vc.make_config(cancel=host_flag.data_ptr()))
+    timer.join()
+    assert e.value.code == -6
+    assert time.time() - t0 < 0.5 * full_s
+    small = G.gnp(60, 0.1, 0)
+    assert vc.mvc(small.offsets, small.neighbors).value == oracle.mvc(small)[0]
