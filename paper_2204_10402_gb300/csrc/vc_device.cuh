@@ -405,12 +405,14 @@ struct Worker {
     // Atomic decrement of d[u] in shared memory.  For 16-bit entries the containing 32-bit word
     // is decremented in the right half; a live vertex with a removed neighbour has degree >= 1, so
     // the half never borrows from its neighbour.
-    __device__ __forceinline__ void dec(int u) {
+    // Returns the new degree.
+    __device__ __forceinline__ int dec(int u) {
         if constexpr (sizeof(W) == 4) {
-            atomicSub(reinterpret_cast<int *>(d) + u, 1);
+            return atomicSub(reinterpret_cast<int *>(d) + u, 1) - 1;
         } else {
             int *word = reinterpret_cast<int *>(d) + (u >> 1);
-            atomicSub(word, (u & 1) ? 0x10000 : 1);
+            const int old = atomicSub(word, (u & 1) ? 0x10000 : 1);
+            return (int)(int16_t)((u & 1) ? (old >> 16) : old) - 1;
         }
     }
 
@@ -431,10 +433,21 @@ struct Worker {
     // changed since that pass last ran, which finds exactly the vertices a full scan would: at the
     // end of a pass every vertex it looked at that still meets its rule has been dealt with, and a
     // vertex whose degree did not change since then kept its live neighbourhood (any removed
-    // neighbour lowers the degree), so it still does not meet the rule.  A root, or a state given
-    // from outside, starts with every vertex dirty; a stored node is a fixpoint of the rules and
-    // starts clean, and its pending removal dirties the neighbours of what it removes.
-    __device__ __forceinline__ void touch(int x) { atomicOr(&dirty[x >> 5], 0x100000001ull << (x & 31)); }
+    // neighbour lowers the degree), so it still does not meet the rule.  A change marks a vertex
+    // only for the pass its new degree concerns (low bit: degree 1; high bit: degree 2): a vertex
+    // of any other degree is no candidate of either pass, and reaching degree 1 or 2 later is
+    // itself a change that marks it.  A root, or a state given from outside, starts with every
+    // vertex dirty; a stored node is a fixpoint of the rules and starts clean, and its pending
+    // removal marks the neighbours of what it removes.
+    __device__ __forceinline__ void touch(int x, int nd) {
+        if (nd == 1 || nd == 2) atomicOr(&dirty[x >> 5], (nd == 1 ? 1ull : 0x100000000ull) << (x & 31));
+    }
+    // Dirty words for the 32 vertices of a chunk from the lanes' new degrees (changed lanes only).
+    static __device__ __forceinline__ unsigned long long dirty_bits(bool changed, int nd) {
+        const unsigned b1 = __ballot_sync(kFull, changed && nd == 1);
+        const unsigned b2 = __ballot_sync(kFull, changed && nd == 2);
+        return (unsigned long long)b1 | ((unsigned long long)b2 << 32);
+    }
     __device__ void dirty_all(int n) {
         for (int i = tid; i < (n + 31) / 32; i += WT) {
             const int rem = n - 32 * i;
@@ -636,8 +649,7 @@ struct Worker {
                 if (marked(x)) {
                     if (x > u) edges++;
                 } else {
-                    dec(x);
-                    touch(x);
+                    touch(x, dec(x));
                     edges++;
                 }
             }
@@ -689,9 +701,13 @@ struct Worker {
 #pragma unroll 1
             for (int k = 0; k < chunks; ++k) {
                 const uint32_t hit = ru[k] & livew[k];  // u itself has no self-loop bit
+                if (hit == 0u) continue;
                 const int v = 32 * k + lane;
-                if ((hit >> lane) & 1u) d[v] = (W)(deg(v) - 1);
-                if (lane == 0 && hit) dirty[k] |= (unsigned long long)hit * 0x100000001ull;
+                const bool mine = (hit >> lane) & 1u;
+                const int nd = mine ? deg(v) - 1 : 0;
+                if (mine) d[v] = (W)nd;
+                const unsigned long long db = dirty_bits(mine, nd);
+                if (lane == 0 && db) dirty[k] |= db;
             }
             if (lane == 0) {
                 d[u] = (W)-1;
@@ -706,6 +722,7 @@ struct Worker {
                 if (k >= chunks) break;
                 const int v = 32 * k + lane;
                 bool changed = false;
+                int nd = -1;
                 if (v < c.n) {
                     const int dv = deg(v);
                     if ((newm[k] >> lane) & 1u) {
@@ -714,7 +731,7 @@ struct Worker {
                     } else if (dv >= 0) {
                         uint32_t b[kNW];
                         row(v, b);
-                        int nd = 0;
+                        nd = 0;
 #pragma unroll
                         for (int w = 0; w < NW; ++w) nd += __popc(b[w] & nl[w]);
                         if (nd != dv) {
@@ -725,8 +742,8 @@ struct Worker {
                         maxd = max(maxd, nd);
                     }
                 }
-                const unsigned chg = __ballot_sync(kFull, changed);
-                if (lane == 0 && chg) dirty[k] |= (unsigned long long)chg * 0x100000001ull;
+                const unsigned long long db = dirty_bits(changed, nd);
+                if (lane == 0 && db) dirty[k] |= db;
             }
             degsum = __reduce_add_sync(kFull, degsum);
             words = __reduce_add_sync(kFull, words);
