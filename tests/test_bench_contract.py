@@ -1,0 +1,36 @@
+"""The benchmark's JSON line (host side, no GPU): the reference arm's keys and that both arms
+name the same workload, metric and unit."""
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_reference_arm_line():
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["value"] > 0 and line["higher_is_better"] is True
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+    sys.path.insert(0, ROOT)
+    import bench
+    assert line["metric"] == bench.METRIC and line["unit"] == "solves/s"
+    assert line["config"]["workload"] == bench.workload_name(bench.NUM_GRAPHS)
+
+
+def test_traffic_figure_follows_the_profiled_sources():
+    # bench.py reports DRAM traffic only while the traversal kernel's sources hash to the value the
+    # committed ncu summary records (null after a kernel change until the next capture).
+    sys.path.insert(0, ROOT)
+    import bench
+    v = bench.measured_per_node("dram_bytes_per_tree_node")
+    assert v is None or v > 0
+    assert bench.measured_per_node("no_such_figure") is None
