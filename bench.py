@@ -356,8 +356,7 @@ def run_ours(a):
     if rank == 0:
         # ---- roofline of the traversal kernel: algorithmic bytes / its event-timed duration ----
         hbm, peak_kind = peaks()
-        # algorithmic bytes: each entry copy at 16 + n*w (the graph's own n) plus 4 bytes per CSR word
-        alg_bytes = [s["entry_bytes_alg"] + 4 * s["csr_words"] for s in stats]
+        alg_bytes = [s["entry_bytes_moved"] + 4 * s["csr_words"] for s in stats]
         ach = [bb / (km * 1e-3) / 1e9 for bb, km in zip(alg_bytes, kernel_ms) if km > 0]
         achieved = statistics.mean(ach) if ach else 0.0
         per_node = measured_per_node("dram_bytes_per_tree_node")

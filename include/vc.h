@@ -126,8 +126,6 @@ typedef struct {
                                    child, [9] stack pops, [10] N(v) children applied by their takers,
                                    [11] acquiring work, [12] solutions; [13]-[15] the number of degree-one,
                                    triangle and high-degree passes; else 0 */
-    int64_t entry_bytes_alg;    /* the same entry copies counted at 16 + n x width bytes each, n the copied
-                                   node's graph (entries are sized for the launch's largest graph) */
 } vc_stats;
 
 /* Minimum Vertex Cover (Sec. II-A, II-B, IV).

@@ -64,8 +64,7 @@ class Stats(ctypes.Structure):
                 ("kernel_ms", ctypes.c_float), ("total_ms", ctypes.c_float),
                 ("trace_ns", ctypes.c_int64 * 4), ("idle_polls", ctypes.c_int64),
                 ("node_in_global", ctypes.c_int32), ("stack_depth", ctypes.c_int32),
-                ("bit_rows", ctypes.c_int32), ("trace_cycles", ctypes.c_int64 * 16),
-                ("entry_bytes_alg", ctypes.c_int64)]
+                ("bit_rows", ctypes.c_int32), ("trace_cycles", ctypes.c_int64 * 16)]
 
     def as_dict(self) -> dict:
         d = {name: getattr(self, name) for name, _ in self._fields_}

@@ -163,7 +163,6 @@ enum TallySlot : int {
     kTPasses,
     kTCsr,
     kTMaxDepth,
-    kTAlgBytes,   // 16 + n * sizeof(W) per entry copied (the graph's own n, no padding)
     kTWaitNs,     // VC_TRACE: time spent waiting for work (worklist, roots, idle)
     kTReduceNs,   // VC_TRACE: reduction rules and stop check
     kTBranchNs,   // VC_TRACE: argmax, donate / push, child construction

@@ -394,7 +394,6 @@ void fill_stats(vc_stats *st, const Result &r, double total_ms, int32_t greedy) 
     st->worker_threads = r.wt;
     st->width = r.width;
     st->csr_staged = r.csr_staged ? 1 : 0;
-    st->entry_bytes_alg = (int64_t)r.ctrl.entry_bytes_alg;
     st->node_in_global = r.gm ? 1 : 0;
     st->bit_rows = r.nw;
     st->stack_depth = r.stack_depth;

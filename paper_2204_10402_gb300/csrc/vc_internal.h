@@ -77,7 +77,6 @@ struct alignas(128) Control {
     unsigned long long stack_pops;
     unsigned long long donations;
     unsigned long long worklist_pops;
-    unsigned long long entry_bytes_alg;  // entry copies at 16 + n * width bytes each (see vc_stats)
     unsigned long long rule_passes;
     unsigned long long csr_words;
     unsigned long long trace_ns[4];  // VC_TRACE builds: ns waiting for work, reducing, branching, solutions

@@ -415,7 +415,6 @@ __global__ void __launch_bounds__(kMaxThreads(WT), kMinBlocks(WT)) traverse_kern
             if constexpr (NW > 0) w.init_live(c);
             if (w.tid == 0) {
                 w.tally[kTPops] += 1;
-                w.tally[kTAlgBytes] += 16u + (unsigned)c.n * sizeof(W);
             }
             VC_CYC_ADD(w, kPPop, t_pop);
         } else {
@@ -442,7 +441,6 @@ __global__ void __launch_bounds__(kMaxThreads(WT), kMinBlocks(WT)) traverse_kern
                 c = make_ctx(P, cur);
                 VC_CHECK(ctrl, c.n >= 0 && c.n <= P.n_max, 14, c.n, { stop = true; break; });
                 w.cur_n = c.n;
-                if (got == 2 && w.tid == 0) w.tally[kTAlgBytes] += 16u + (unsigned)c.n * sizeof(W);
                 w.template stage<false>(c, rows_of<NW>(P, c));
                 if constexpr (NW > 0) w.init_live(c);
             }
@@ -534,7 +532,6 @@ __global__ void __launch_bounds__(kMaxThreads(WT), kMinBlocks(WT)) traverse_kern
                         st_release_u32(&P.wl_seq[pos & wl_mask], pos + 1u);
                         atomicAdd(&ctrl->wl_count, 1);
                         w.tally[kTDonations] += 1;
-                        w.tally[kTAlgBytes] += 16u + (unsigned)c.n * sizeof(W);
                     }
                 } else {  // push on the local stack
                     if (top >= P.stack_depth) {
@@ -546,7 +543,6 @@ __global__ void __launch_bounds__(kMaxThreads(WT), kMinBlocks(WT)) traverse_kern
                     ++top;
                     if (w.tid == 0) {
                         w.tally[kTPushes] += 1;
-                        w.tally[kTAlgBytes] += 16u + (unsigned)c.n * sizeof(W);
                         if ((unsigned long long)top > w.tally[kTMaxDepth]) w.tally[kTMaxDepth] = top;
                     }
                     w.sync();
@@ -569,7 +565,6 @@ __global__ void __launch_bounds__(kMaxThreads(WT), kMinBlocks(WT)) traverse_kern
         atomicAdd(&ctrl->stack_pops, T[kTPops]);
         atomicAdd(&ctrl->donations, T[kTDonations]);
         atomicAdd(&ctrl->worklist_pops, T[kTDequeues]);
-        atomicAdd(&ctrl->entry_bytes_alg, T[kTAlgBytes]);
         atomicAdd(&ctrl->rule_passes, T[kTPasses]);
         atomicAdd(&ctrl->csr_words, T[kTCsr]);
 #ifdef VC_TRACE

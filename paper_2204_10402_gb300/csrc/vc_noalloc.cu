@@ -211,7 +211,6 @@ extern "C" int vc_mvc_noalloc(const vc_graph *g, const vc_config *cfg_in, void *
         stats->csr_words = (int64_t)h_ctrl.csr_words;
         stats->entry_bytes_moved = (int64_t)eb * (int64_t)(h_ctrl.stack_pops + h_ctrl.stack_pushes + h_ctrl.donations +
                                                             h_ctrl.worklist_pops);
-        stats->entry_bytes_alg = (int64_t)h_ctrl.entry_bytes_alg;
         stats->max_depth = h_ctrl.max_depth;
         stats->greedy_ub = h_res.greedy;
         stats->workers = (int32_t)workers;

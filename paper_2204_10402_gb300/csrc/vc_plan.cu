@@ -266,7 +266,6 @@ int vc_plan_results(vc_plan *pl, void *stream, int32_t *sizes_out, int32_t *cove
         stats->worker_threads = pl->wt;
         stats->width = pl->width;
         stats->bit_rows = pl->nw;
-        stats->entry_bytes_alg = (int64_t)c.entry_bytes_alg;
         stats->status = c.status;
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, pl->ev0, pl->ev1) == cudaSuccess) stats->kernel_ms = ms;

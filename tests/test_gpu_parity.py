@@ -262,10 +262,6 @@ def test_batch_matches_oracle(vc):
         assert sizes[i] == want, i
         check_cover(g, covers[b.vtx[i]: b.vtx[i + 1]], want)
     assert st["nodes_visited"] > 0
-    # copies counted at the copied graph's own size never exceed the padded entries moved
-    copies = st["stack_pops"] + st["stack_pushes"] + st["donations"] + st["worklist_pops"]
-    assert 0 < st["entry_bytes_alg"] <= st["entry_bytes_moved"]
-    assert st["entry_bytes_alg"] >= copies * (16 + 4 * min(g.n for g in b.graphs))
 
 
 @pytest.mark.parametrize("bit_rows", [1, -1])
