@@ -234,12 +234,17 @@ def test_config_gnp60(vc):
 
 
 def test_config_chung_lu_2000_pvc(vc):
+    # Table I's PVC columns: k = min (yes), k = min - 1 (no: the whole tree), k = min + 1 (yes).
     g = G.chung_lu(2000, 6.0, 0)
     best, _, _ = oracle.mvc(g)
     yes = vc.pvc(g.offsets, g.neighbors, best)
     no = vc.pvc(g.offsets, g.neighbors, best - 1)
     assert yes.value == 1 and no.value == 0
     check_cover(g, yes.cover, yes.cover_size)
+    assert yes.cover_size <= best
+    above = vc.pvc(g.offsets, g.neighbors, best + 1)
+    assert above.value == 1 and above.cover_size <= best + 1
+    check_cover(g, above.cover, above.cover_size)
     m = vc.mvc(g.offsets, g.neighbors)
     assert m.value == best
 
