@@ -187,9 +187,10 @@ int vc_reduce_node(const vc_graph *g, int32_t *deg, int32_t *S, int32_t *m, int3
  *     *cover_size_out (host) receive the result; cfg and stats may be NULL.
  *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
  *     that device current; make that first call before capturing any stream.
- *   - All calls share the one array and each call resets what must start from a known value.
- *     Calls whose GPU work overlaps (other streams, other host threads without ordering) race on
- *     it; the library serialises calls from one process only on the host side.
+ *   - All calls of a process share the one array, and each call resets what must start from a
+ *     known value.  Calls are serialised: each holds a process-wide lock until its GPU work has
+ *     finished, error returns included, so calls from any host threads and streams of one process
+ *     never overlap on the array.  Each process has its own array.
  *   - The call synchronises `stream` twice (after the greedy bound, which sizes the stacks, and at
  *     the end). */
 #define VC_NOALLOC_MAX_N 512

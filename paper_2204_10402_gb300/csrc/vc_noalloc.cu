@@ -90,6 +90,14 @@ extern "C" int vc_mvc_noalloc(const vc_graph *g, const vc_config *cfg_in, void *
     cudaStream_t s = (cudaStream_t)stream;
 
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    // Every return, error paths included, waits for this call's GPU work before the lock is
+    // released (declared after the lock, so it runs first): the next call never overlaps it.
+    struct DrainOnExit {
+        cudaStream_t s;
+        ~DrainOnExit() {
+            if (cudaStreamSynchronize(s) != cudaSuccess) cudaGetLastError();
+        }
+    } drain{s};
     uint8_t *base = nullptr;
     int sms = 0;
     if (int rc = scratch_for_current_device(&base, &sms)) return rc;

@@ -57,3 +57,36 @@ def test_noalloc_rejects_oversize_and_host_inputs(vc):
     g = G.petersen()
     with pytest.raises(ValueError):
         vc.mvc_noalloc(g.offsets, g.neighbors)
+
+
+def test_noalloc_calls_from_several_threads_are_serialised(vc):
+    # Four host threads, each on its own stream, call concurrently (ctypes releases the GIL); the
+    # library serialises them on the one scratch array, so every answer equals the oracle's.
+    import threading
+    import torch
+    gs = graphs()[:6]
+    want = [oracle.mvc(g)[0] for g in gs]
+    dev = [(torch.from_numpy(g.offsets).cuda(), torch.from_numpy(g.neighbors).cuda()) for g in gs]
+    torch.cuda.synchronize()
+    errors = []
+
+    def work(t):
+        try:
+            s = torch.cuda.Stream()
+            for _ in range(3):
+                for i in range(len(gs)):
+                    j = (i + t) % len(gs)
+                    a = vc.mvc_noalloc(*dev[j], stream=s)
+                    cover = a.cover.cpu().numpy().astype(bool)
+                    if a.value != want[j] or cover.sum() != a.value or not oracle.verify_cover(gs[j], cover):
+                        errors.append((t, j, a.value, want[j]))
+        except Exception as e:  # reported below, in the test's own thread
+            errors.append((t, repr(e)))
+
+    threads = [threading.Thread(target=work, args=(t,)) for t in range(4)]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join(timeout=120)
+    assert not any(th.is_alive() for th in threads)
+    assert not errors, errors
