@@ -18,6 +18,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -94,11 +95,31 @@ TRAVERSAL_SOURCES = ("vc_internal.h", "vc_device.cuh", "vc_kernels.cuh", "vc_lau
                      "vc_kern_w16_rows.cu", "vc_kern_w32_rows.cu")
 
 
+def code_only(text: str) -> str:
+    """C/C++/CUDA source without its comments, indentation or blank lines (no string literal in
+    the traversal sources contains a comment marker)."""
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return "\n".join(line.strip() for line in text.splitlines() if line.strip())
+
+
+def traversal_source_hash(csrc: str | None = None) -> str:
+    """Hash of the traversal kernel's code: a change of code anywhere in TRAVERSAL_SOURCES changes
+    it, a change of comments or layout does not."""
+    import hashlib
+    csrc = csrc or os.path.join(ROOT, "paper_2204_10402_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in TRAVERSAL_SOURCES:
+        h.update(f.encode())
+        with open(os.path.join(csrc, f), encoding="utf-8") as fh:
+            h.update(code_only(fh.read()).encode())
+    return h.hexdigest()[:16]
+
+
 def measured_per_node(key: str = "dram_bytes_per_tree_node"):
     """A per-tree-node figure of the traversal kernel (DRAM bytes, warp instructions) from the
-    committed ncu summary, or None when the kernel sources changed since that capture (the
-    summary records their hash)."""
-    import hashlib
+    committed ncu summary, or None when the kernel's code changed since that capture (the
+    summary records its hash)."""
     path = os.path.join(ROOT, "profiles", "traverse_kernel_batch_gnp.md")
     if not os.path.exists(path):
         return None
@@ -107,13 +128,7 @@ def measured_per_node(key: str = "dram_bytes_per_tree_node"):
         if ":" in line and line.split(":")[0] in ("kernel_source_hash", key):
             k, v = line.split(":", 1)
             rec[k] = v.strip()
-    csrc = os.path.join(ROOT, "paper_2204_10402_gb300", "csrc")
-    h = hashlib.sha256()
-    for f in TRAVERSAL_SOURCES:
-        h.update(f.encode())
-        with open(os.path.join(csrc, f), "rb") as fh:
-            h.update(fh.read())
-    if rec.get("kernel_source_hash") != h.hexdigest()[:16] or key not in rec:
+    if rec.get("kernel_source_hash") != traversal_source_hash() or key not in rec:
         return None
     return float(rec[key])
 

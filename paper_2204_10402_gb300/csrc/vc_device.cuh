@@ -5,8 +5,9 @@
 // Shared-memory layout of a worker (all offsets 16-byte aligned):
 //   [entry]  EntryHeader (16 B) + degree array W[n_max] padded to 16 B   <- copied to/from stacks
 //   [marks]  CSR-walk workers: one bit per vertex, chosen for S in the current pass
-//   [dirty]  one 64-bit word per 32 vertices: low half = degree changed since the degree-one pass
-//            last looked at the vertex, high half = the same for the degree-two-triangle pass
+//   [dirty]  one 64-bit word per 32 vertices: low half = degree changed to one since the degree-one
+//            pass last looked at the vertex, high half = changed to two since the degree-two-triangle
+//            pass last looked at it
 //   [list]   CSR-walk workers: int32[n_max], the vertices chosen in the current pass (each once)
 //   [sc]     kScratchWords int32: tallies, broadcasts, per-warp reduction keys, trace slots
 //   [csr]    optional copy of the current graph's CSR (offsets, then neighbours), so that the
@@ -675,11 +676,13 @@ struct Worker {
 
     // ---- bit-row removal and rules (NW > 0) -------------------------------------------------------
 
-    // Moves the chosen set newm into S: every live vertex outside it gets its degree recomputed as
-    // popc(row & live'), a vertex whose degree changed is marked dirty for both passes, and
-    // m = (sum of live degrees) / 2.  Same result as apply_list's decrements.  (The loops over
-    // 32-vertex chunks are kept rolled and read the chunk's mask words from shared memory: the
-    // traversal is sensitive to its code size.)
+    // Moves the chosen set newm into S.  One chosen vertex u (the "v" child and most single rule
+    // removals): u's live neighbours lose one degree each and m loses deg(u).  Several: every live
+    // vertex outside the set gets its degree recomputed as popc(row & live'), and m = (sum of live
+    // degrees) / 2.  Either way a vertex whose degree changed to one or two is marked dirty for the
+    // pass that degree concerns, and the result equals apply_list's decrements.  (The
+    // single-vertex loop over 32-vertex chunks stays rolled and the general one is unrolled: each
+    // measured fastest, the traversal being sensitive to its code size.)
     __device__ void apply_rows(const Ctx &c) {
         __syncwarp();  // every proposal (shared atomics) is done
         uint32_t nl[kNW];

@@ -34,3 +34,23 @@ def test_traffic_figure_follows_the_profiled_sources():
     v = bench.measured_per_node("dram_bytes_per_tree_node")
     assert v is None or v > 0
     assert bench.measured_per_node("no_such_figure") is None
+
+
+def test_source_hash_follows_code_not_comments(tmp_path):
+    # The profile stays matched when only comments or layout change, and not when code changes.
+    import shutil
+    sys.path.insert(0, ROOT)
+    import bench
+    src = os.path.join(ROOT, "paper_2204_10402_gb300", "csrc")
+    copy = tmp_path / "csrc"
+    shutil.copytree(src, copy)
+    base = bench.traversal_source_hash(str(copy))
+    assert base == bench.traversal_source_hash()
+    dev = copy / "vc_device.cuh"
+    text = dev.read_text()
+    dev.write_text("// a new comment\n/* and a block\n   comment */\n\n" + text.replace("\n", "\n\n", 5))
+    assert bench.traversal_source_hash(str(copy)) == base
+    anchor = "constexpr unsigned kFull = 0xffffffffu;"
+    assert anchor in text
+    dev.write_text(text.replace(anchor, "constexpr unsigned kFull = 0x7fffffffu;"))
+    assert bench.traversal_source_hash(str(copy)) != base
