@@ -381,7 +381,7 @@ def run_ours(a):
         roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                     "frac": achieved / hbm,
                     "traffic": per_node * nodes_per_launch if per_node is not None else None,
-                    "traffic_note": "ncu dram bytes per tree node (512-graph capture) x nodes of this launch",
+                    "traffic_note": "ncu dram bytes per tree node of the full 4096-graph launch (1 pass) x nodes of this launch",
                     "peak_kind": peak_kind, "kernel": "traverse_kernel",
                     "kernel_ms_mean": statistics.mean(kernel_ms),
                     "alg_bytes_per_launch": statistics.mean(alg_bytes),
