@@ -397,7 +397,7 @@ def run_ours(a):
             peak_ginst = sms * 4 * mhz / 1e3
             roofline["issue"] = {"achieved": ginst, "peak": peak_ginst, "unit": "G warp-inst/s",
                                  "frac": ginst / peak_ginst if peak_ginst else None,
-                                 "note": "ncu warp instructions per tree node x nodes / kernel time; "
+                                 "note": "ncu warp instructions per tree node (full 4096-graph launch) x nodes / kernel time; "
                                          "peak = SMs x 4 schedulers x sampled SM clock"}
         line = {
             "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": a.steps,
