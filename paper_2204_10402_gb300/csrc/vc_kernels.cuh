@@ -378,7 +378,7 @@ __device__ int acquire(const Params &P, Worker<W, WT, GM, NW> &w) {
 // four workers per block (40 to 64 warps per SM) ran 171, 180 and 250 ms against 171 ms for the
 // same build at 64 registers.
 constexpr int kMaxThreads(int wt) { return wt == 32 ? 64 : wt; }
-constexpr unsigned kSnapshotEvery = 4;  // nodes per re-read of the shared bounds (a power of two)
+constexpr unsigned kSnapshotEvery = 16;  // nodes per re-read of the shared bounds (a power of two)
 constexpr int kMinBlocks(int wt) { return wt == 32 ? 16 : 1024 / wt; }
 // SERVE: the launch also takes requests from a server's ring (the instance the server launches);
 // batch launches use the instance without that path, which keeps their code smaller.
@@ -456,9 +456,10 @@ __global__ void __launch_bounds__(kMaxThreads(WT), kMinBlocks(WT)) traverse_kern
         // ---- expand nodes, continuing into the "v" child after each branch ----
         for (;;) {
             const long long t_hdr = VC_CYC();
-            // The snapshot of best / found / status / worklist fill is re-read for every fourth node
+            // The snapshot of best / found / status / worklist fill is re-read for every 16th node
             // and for the first node after acquiring work (reading R3: a stale, larger best only
-            // weakens pruning).  Re-reading it for every node cost 2 % of the batch time.
+            // weakens pruning).  Re-reading it for every node cost 2.5 % of the batch time, and for
+            // every fourth node 0.5 %.
             if (w.tid == 0) {
                 const unsigned long long nn = ++w.tally[kTNodes];
                 if ((nn & 31) == 0) atomicAdd(&ctrl->heartbeat, 1u);
