@@ -367,6 +367,37 @@ def test_batch_multiwarp_workers(vc, wt):
         assert [int(x) for x in sizes] == [want[i][2] for i in range(1024)]
 
 
+def test_batch_with_degenerate_members(vc):
+    # A ragged batch: empty and edgeless graphs, a single edge, closed forms and ordinary graphs
+    # side by side (through vc_mvc_batch and a batch plan); batches of one graph, of empty graphs
+    # only, and of no graph.
+    import torch
+    empty = G.csr_from_edges(0, [], [])
+    members = [empty, G.csr_from_edges(7, [], []), G.path(2), G.petersen(), G.gnp(60, 0.10, 0), empty,
+               G.complete(5), G.star(8), G.gnp(120, 0.3, 7, draw_offset=2), G.csr_from_edges(1, [], [])]
+    want = [oracle.mvc(g)[0] for g in members]
+    assert want[:4] == [0, 0, 1, 6] and want[6:8] == [4, 1]
+    b = G.pack(members)
+    sizes, covers, _ = vc.mvc_batch(b.vtx, b.edge, b.offsets, b.neighbors)
+    assert [int(x) for x in sizes] == want
+    for i, g in enumerate(members):
+        check_cover(g, covers[b.vtx[i]: b.vtx[i + 1]], want[i])
+    plan = vc.BatchPlan(b.vtx, b.edge, torch.from_numpy(b.offsets).cuda(), torch.from_numpy(b.neighbors).cuda())
+    plan.launch()
+    psizes, pcovers, _ = plan.results(want_covers=True)
+    plan.close()
+    assert [int(x) for x in psizes] == want
+    for i, g in enumerate(members):
+        check_cover(g, pcovers[b.vtx[i]: b.vtx[i + 1]], want[i])
+    for group in ([G.petersen()], [empty], [empty, G.csr_from_edges(3, [], []), empty]):
+        pb = G.pack(group)
+        s2, c2, _ = vc.mvc_batch(pb.vtx, pb.edge, pb.offsets, pb.neighbors)
+        assert [int(x) for x in s2] == [oracle.mvc(g)[0] for g in group]
+    s0, _, _ = vc.mvc_batch(np.zeros(1, np.int32), np.zeros(1, np.int32), np.zeros(0, np.int32),
+                            np.zeros(0, np.int32))
+    assert s0.size == 0
+
+
 def test_batch_plan_graph_replay(vc):
     # The batch captured as one CUDA graph, replayed three times: identical answers every time,
     # equal to the oracle's, with valid covers.
