@@ -511,9 +511,9 @@ int vc_server_submit(vc_server *s, const vc_graph *g, int32_t kind, int32_t k, u
         delete r;
         return VC_EINVAL;
     }
-    r->off.assign(g->offsets, g->offsets + g->n + 1);
-    if (g->n == 0) r->off.assign(1, 0);
-    r->adj.assign(g->neighbors, g->neighbors + len);
+    if (g->n == 0) r->off.assign(1, 0);  // offsets may be null for an empty graph
+    else r->off.assign(g->offsets, g->offsets + g->n + 1);
+    if (len > 0) r->adj.assign(g->neighbors, g->neighbors + len);
     r->bytes = up(sizeof(int32_t) * ((size_t)r->n + 1)) + up(sizeof(int32_t) * std::max<size_t>(len, 1)) +
                up(sizeof(int32_t) * std::max<size_t>(r->n, 1));
     if (r->bytes > s->arena_bytes) {

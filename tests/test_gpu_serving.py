@@ -110,3 +110,24 @@ def test_rejects_bad_requests(vc):
         rid = srv.submit(g.offsets, g.neighbors, 0)
         srv.drain(timeout_ms=60000)
         assert srv.poll(rid)["answer"] == 3
+
+
+def test_degenerate_requests(vc):
+    # Empty and edgeless graphs, k >= n, k just below and at the minimum, and an empty graph given
+    # with null arrays through the C ABI: answers as the definitions give them (MVC(K5) = 4,
+    # MVC(P2) = 1, an edgeless graph needs no vertex).
+    import ctypes
+    empty = G.csr_from_edges(0, [], [])
+    edgeless = G.csr_from_edges(6, [], [])
+    k5, p2 = G.complete(5), G.path(2)
+    cases = [(empty, 0, 0, 0), (empty, 1, 0, 1), (edgeless, 0, 0, 0), (edgeless, 1, 0, 1),
+             (k5, 1, 10, 1), (k5, 1, 3, 0), (k5, 0, 0, 4), (p2, 1, 0, 0), (p2, 1, 1, 1)]
+    with vc.Server(max_n=50) as srv:
+        ids = [srv.submit(g.offsets, g.neighbors, kind, k) for g, kind, k, _ in cases]
+        raw = vc.Graph(0, None, None, 0)
+        rid = ctypes.c_uint64(0)
+        assert srv._lib.vc_server_submit(srv._h, ctypes.byref(raw), 0, 0, ctypes.byref(rid)) == 0
+        srv.drain(timeout_ms=60000)
+        infos = [srv.poll(i) for i in ids] + [srv.poll(rid.value)]
+    assert all(x["done"] and x["status"] == 0 for x in infos)
+    assert [x["answer"] for x in infos] == [c[3] for c in cases] + [0]
