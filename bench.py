@@ -32,7 +32,7 @@ sys.path.insert(0, ROOT)
 METRIC = "search-tree nodes/sec and solves/sec (p50/p99 latency) vs plain launches; % L2/HBM roofline"
 NUM_GRAPHS = 4096
 L2_FLUSH_BYTES = 256 << 20
-CPU_SAMPLE_GRAPHS = 128
+CPU_SAMPLE_GRAPHS = 256  # about 15 s of single-core oracle work
 PLAIN_SAMPLE_GRAPHS = 512
 # Kernels in one replay of the batch plan: worklist init, greedy bound, traversal, answer gather.
 KERNELS_PER_STEP = 4
@@ -430,7 +430,7 @@ def run_ours(a):
             seeds = list(range(min(CPU_SAMPLE_GRAPHS, G)))
             secs = oracle_solves(seeds, 1)
             line["cpu_baseline"] = {"value": len(seeds) / secs, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                                    "sample": f"first {len(seeds)} graphs of the batch, one core"}
+                                    "sample": f"first {len(seeds)} graphs of the batch, one core, {secs:.1f} s"}
         out = line
         print(json.dumps(line), flush=True)
     if world > 1:
