@@ -58,8 +58,8 @@ extern "C" {
 /* An undirected graph in CSR form (see the input rules above). */
 typedef struct {
     int32_t n;                 /* number of vertices, >= 0 */
-    const int32_t *offsets;    /* n+1 entries */
-    const int32_t *neighbors;  /* offsets[n] entries */
+    const int32_t *offsets;    /* n+1 entries (may be NULL when n = 0) */
+    const int32_t *neighbors;  /* offsets[n] entries (may be NULL when there are none) */
     int32_t on_device;         /* 0: host pointers, 1: device pointers */
 } vc_graph;
 

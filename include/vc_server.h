@@ -59,7 +59,11 @@ typedef struct {
  * width, worklist capacity and donation threshold as in vc.h. */
 int vc_server_create(const vc_config *cfg, size_t device_bytes_budget, int32_t max_n, vc_server **server);
 
-/* Queues a request: kind 0 = MVC, 1 = PVC with parameter k.  Returns at once with its id. */
+/* Queues a request: kind 0 = MVC, 1 = PVC with parameter k.  Returns at once with its id.  The
+ * graph must be on the host (on_device = 0) with n <= max_n; it is copied before the call returns,
+ * so the caller may free it then.  The CSR is checked on the host against the rules of vc.h (the
+ * running launch never sees a malformed graph), and a malformed one is rejected here with
+ * VC_EINVAL.  PVC with k < 0 is answered at once (no). */
 int vc_server_submit(vc_server *server, const vc_graph *g, int32_t kind, int32_t k, uint64_t *request_id);
 
 /* Reads a request's state (see vc_request_info). */

@@ -304,8 +304,11 @@ bool csr_ok(const vc_graph *g) {
     if (n == 0) return true;
     const int32_t *off = g->offsets, *adj = g->neighbors;
     if (off[0] != 0 || off[n] < 0 || (off[n] & 1) || (off[n] > 0 && !adj)) return false;
-    for (int32_t v = 0; v < n; ++v) {
+    // Every offset is checked before any list is read: the symmetry test below searches the
+    // lists of later vertices.
+    for (int32_t v = 0; v < n; ++v)
         if (off[v + 1] < off[v] || off[v + 1] > off[n]) return false;
+    for (int32_t v = 0; v < n; ++v) {
         for (int32_t j = off[v]; j < off[v + 1]; ++j) {
             const int32_t x = adj[j];
             if (x < 0 || x >= n || x == v || (j > off[v] && adj[j - 1] >= x)) return false;

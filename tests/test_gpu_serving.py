@@ -105,6 +105,10 @@ def test_rejects_bad_requests(vc):
         bad[0] = 4
         with pytest.raises(vc.VCError):
             srv.submit(g.offsets, bad, 0)
+        off = g.offsets.copy()
+        off[5] = off[6] + 8                 # a later vertex's range runs past the neighbour list
+        with pytest.raises(vc.VCError):
+            srv.submit(off, g.neighbors, 0)
         rid = srv.submit(g.offsets, g.neighbors, 1, -1)   # k < 0 is answered at once
         assert srv.poll(rid)["done"] == 1 and srv.poll(rid)["answer"] == 0
         rid = srv.submit(g.offsets, g.neighbors, 0)
