@@ -168,9 +168,20 @@ Problem make_problem(int64_t off_base, int64_t adj_base, int64_t cover_base, int
     return p;
 }
 
+// Waits for a call's queued work on every return, error paths included.  Declared after the
+// workspace lock, it runs before the lock is released: the workspace is the next call's then, so
+// nothing may still run on it.
+struct StreamDrain {
+    cudaStream_t s;
+    ~StreamDrain() {
+        if (cudaStreamSynchronize(s) != cudaSuccess) cudaGetLastError();
+    }
+};
+
 // Runs one launch.  cover_out (may be null) receives Σ n cover entries, on the device or host.
 int run(Workspace &ws, const Spec &spec, const vc_config *cfg_in, cudaStream_t s, int32_t *cover_out,
         int cover_on_device, Result &res) {
+    StreamDrain drain{s};
     vc_config cfg;
     std::memset(&cfg, 0, sizeof(cfg));
     if (cfg_in) cfg = *cfg_in;
@@ -592,6 +603,7 @@ int vc_reduce_node(const vc_graph *g, int32_t *deg, int32_t *S, int32_t *m, int3
     if (c.bit_rows > 0 && nw == 0) return VC_EINVAL;
     if (nw > 0) smem = smem_bytes_for(g->n, width / 8, 0, nw);
     cudaStream_t s = (cudaStream_t)stream;
+    StreamDrain drain{s};
     const int64_t len = g->on_device ? -1 : g->offsets[g->n];
     // device copies: graph (if host), degree array, io words
     const size_t deg_bytes = sizeof(int32_t) * (size_t)g->n;
