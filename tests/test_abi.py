@@ -1,7 +1,10 @@
-"""The C ABI library loads and exports every entry point that include/vc.h declares (no GPU)."""
+"""The C ABI library loads and exports every entry point that include/vc.h declares, a missing
+library is an error rather than a fallback, and the package never loads the oracle (no GPU)."""
 import ctypes
 import os
 import re
+import subprocess
+import sys
 
 import pytest
 
@@ -78,3 +81,36 @@ def test_struct_layouts_match_binding(tmp_path, type_name, header, cls):
     size, offsets = _c_layout(tmp_path, type_name, fields, header)
     assert ctypes.sizeof(py) == size
     assert [getattr(py, f).offset for f in fields] == offsets
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    # No CPU fallback: a solve without libvc.so raises instead of computing anything.
+    missing = str(tmp_path / "libvc.so")
+    code = ("import paper_2204_10402_gb300 as vc\n"
+            "from paper_2204_10402_gb300 import graphs as G\n"
+            f"vc.LIB_PATH = {missing!r}\n"
+            "g = G.path(3)\n"
+            "try:\n"
+            "    vc.mvc(g.offsets, g.neighbors)\n"
+            "except ImportError:\n"
+            "    print('raised')\n")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert r.stdout.strip() == "raised"
+
+
+def test_product_path_does_not_touch_the_oracle():
+    # The oracle is test infrastructure: importing the package and its modules never loads it,
+    # and no module of the package names it in an import.
+    code = ("import sys\n"
+            "import paper_2204_10402_gb300\n"
+            "from paper_2204_10402_gb300 import graphs, autotune, build\n"
+            "print('oracle' in sys.modules)\n")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert r.stdout.strip() == "False"
+    pkg = os.path.join(ROOT, "paper_2204_10402_gb300")
+    for name in os.listdir(pkg):
+        if name.endswith(".py"):
+            text = open(os.path.join(pkg, name)).read()
+            assert "import oracle" not in text and "from oracle" not in text, name
