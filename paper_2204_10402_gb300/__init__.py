@@ -164,9 +164,16 @@ def _is_cuda_tensor(x) -> bool:
 
 
 def _host_i32(x) -> np.ndarray:
+    """A host int32 copy (or view) of an integer array; values outside int32 are an error, not a
+    silent wrap."""
     if hasattr(x, "detach"):
         x = x.detach().cpu().numpy()
-    return np.ascontiguousarray(np.asarray(x), dtype=np.int32)
+    a = np.asarray(x)
+    if a.size and not np.issubdtype(a.dtype, np.integer):
+        raise TypeError(f"CSR arrays must hold integers, not {a.dtype}")
+    if a.dtype != np.int32 and a.size and (int(a.min()) < -2**31 or int(a.max()) >= 2**31):
+        raise ValueError("CSR values do not fit int32")
+    return np.ascontiguousarray(a, dtype=np.int32)
 
 
 def _ptr(x) -> int:
@@ -201,16 +208,27 @@ def make_config(**kw) -> Config:
     return c
 
 
+def _device_csr(offsets, neighbors):
+    """Contiguous int32 CUDA tensors of a CSR on the current device, which the library launches on.
+    The caller keeps them alive until the library call has returned."""
+    import torch
+    if not _is_cuda_tensor(neighbors) or neighbors.device != offsets.device:
+        raise ValueError("offsets and neighbors must be CUDA tensors on the same device")
+    if offsets.device.index != torch.cuda.current_device():
+        raise ValueError(f"the CSR is on {offsets.device} but the current device is "
+                         f"cuda:{torch.cuda.current_device()}; call under torch.cuda.device({offsets.device})")
+    if offsets.dtype != torch.int32 or neighbors.dtype != torch.int32:
+        raise TypeError("CSR tensors must be int32")
+    off = offsets.contiguous()
+    nb = neighbors.contiguous() if neighbors.numel() > 0 else torch.zeros(1, dtype=torch.int32, device=offsets.device)
+    return off, nb
+
+
 def _graph(offsets, neighbors):
     """Returns (Graph, keepalive) for host numpy or CUDA tensor CSR arrays."""
     if _is_cuda_tensor(offsets):
-        import torch
-        assert offsets.dtype == torch.int32 and neighbors.dtype == torch.int32, "CSR tensors must be int32"
-        offsets = offsets.contiguous()
-        neighbors = neighbors.contiguous()
-        n = offsets.numel() - 1
-        nb = neighbors if neighbors.numel() > 0 else torch.zeros(1, dtype=torch.int32, device=offsets.device)
-        return Graph(n, offsets.data_ptr(), nb.data_ptr(), 1), (offsets, nb)
+        off, nb = _device_csr(offsets, neighbors)
+        return Graph(off.numel() - 1, off.data_ptr(), nb.data_ptr(), 1), (off, nb)
     off = _host_i32(offsets)
     nbr = _host_i32(neighbors)
     if nbr.size == 0:
@@ -295,8 +313,7 @@ def mvc_batch(vtx, edge, offsets, neighbors, config: Config | None = None, strea
     on_dev = _is_cuda_tensor(offsets)
     if on_dev:
         import torch
-        off_t = offsets.contiguous()
-        nb_t = neighbors.contiguous() if neighbors.numel() else torch.zeros(1, dtype=torch.int32, device=offsets.device)
+        off_t, nb_t = _device_csr(offsets, neighbors)
         off_p, nb_p = off_t.data_ptr(), nb_t.data_ptr()
         covers = torch.empty(max(int(vtx[-1]), 1), dtype=torch.int32, device=offsets.device) if want_covers else None
     else:
@@ -363,7 +380,8 @@ def last_sm_nodes() -> np.ndarray:
 def l2_copy_probe(dst, src, passes: int, stream=None):
     """Copies CUDA tensor src onto dst `passes` times in one launch through L2 (measurement
     helper; see vc_l2_copy_probe).  Returns without waiting for the stream."""
-    assert _is_cuda_tensor(dst) and _is_cuda_tensor(src) and dst.numel() * dst.element_size() == src.numel() * src.element_size()
+    if not (_is_cuda_tensor(dst) and _is_cuda_tensor(src)) or dst.numel() * dst.element_size() != src.numel() * src.element_size():
+        raise ValueError("l2_copy_probe takes two CUDA tensors of the same size in bytes")
     _check(load().vc_l2_copy_probe(dst.data_ptr(), src.data_ptr(), src.numel() * src.element_size(), int(passes),
                                    _stream(stream)), "vc_l2_copy_probe")
 
@@ -446,8 +464,8 @@ class BatchPlan:
         self.total_n = int(vtx[-1])
         on_dev = _is_cuda_tensor(offsets)
         if on_dev:
-            off_p = offsets.contiguous().data_ptr()
-            nb_p = neighbors.contiguous().data_ptr() if neighbors.numel() else 0
+            off_t, nb_t = _device_csr(offsets, neighbors)  # held until the plan has copied them
+            off_p, nb_p = off_t.data_ptr(), nb_t.data_ptr()
         else:
             o = _host_i32(offsets)
             nbr = _host_i32(neighbors)

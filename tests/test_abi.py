@@ -114,3 +114,20 @@ def test_product_path_does_not_touch_the_oracle():
         if name.endswith(".py"):
             text = open(os.path.join(pkg, name)).read()
             assert "import oracle" not in text and "from oracle" not in text, name
+
+
+def test_host_csr_arrays_are_checked_not_wrapped():
+    # Host CSR arrays become int32 copies; values outside int32 and non-integer arrays are errors
+    # instead of silently wrapped or truncated inputs.
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import paper_2204_10402_gb300 as vc
+    ok = vc._host_i32(np.array([0, 2, 4], dtype=np.int64))
+    assert ok.dtype == np.int32 and ok.tolist() == [0, 2, 4]
+    assert vc._host_i32([]).size == 0
+    with pytest.raises(ValueError):
+        vc._host_i32(np.array([0, 2**31], dtype=np.int64))
+    with pytest.raises(ValueError):
+        vc._host_i32(np.array([-2**31 - 1, 0], dtype=np.int64))
+    with pytest.raises(TypeError):
+        vc._host_i32(np.array([0.0, 1.5]))
