@@ -9,6 +9,7 @@
 - tree_mvc: the textbook dynamic programme over a rooted tree (each vertex either in the cover,
   or out of it with all its children in).
 - load_rule_cases: parses tests/golden/rules.txt.
+- load_greedy_cases: parses tests/golden/greedy.txt (hand-derived greedy bounds and covers).
 """
 from __future__ import annotations
 
@@ -111,6 +112,33 @@ def load_rule_cases(path: str | None = None) -> list:
                 cur[key] = [int(x) for x in rest.split()]
             elif key in ("start_S", "start_m", "expect_S", "expect_m", "expect_pruned"):
                 cur[key] = int(rest)
+            else:
+                raise ValueError(f"unknown field {key!r} in {path}")
+    return cases
+
+
+def load_greedy_cases(path: str | None = None) -> list:
+    path = path or os.path.join(GOLDEN, "greedy.txt")
+    cases, cur = [], None
+    with open(path) as f:
+        for raw in f:
+            line = raw.strip()
+            if not line or line.startswith("#"):
+                continue
+            key, _, rest = line.partition(" ")
+            if key == "case":
+                cur = {"name": rest}
+                cases.append(cur)
+            elif key == "cite":
+                cur["cite"] = rest
+            elif key == "n":
+                cur["n"] = int(rest)
+            elif key == "edges":
+                cur["edges"] = [tuple(int(x) for x in e.split("-")) for e in rest.split()]
+            elif key == "expect_greedy":
+                cur["expect_greedy"] = int(rest)
+            elif key == "expect_cover":
+                cur["expect_cover"] = sorted(int(x) for x in rest.split())
             else:
                 raise ValueError(f"unknown field {key!r} in {path}")
     return cases

@@ -42,6 +42,11 @@ MUTANTS = [
      "if (x->deg[g->adj[e]] != REMOVED) s->mark[g->adj[e]] = 1;", ";"),
     ("PVC greedy shortcut accepts a cover one too large",
      "if (u <= k) { /* reading R6 */", "if (u <= k + 1) { /* reading R6 */"),
+    ("maximum-degree ties go to the highest id",
+     "        if (x->deg[v] > best_d) {", "        if (x->deg[v] >= best_d) {"),
+    ("greedy skips the degree-two-triangle rule",
+     "        reduce(&g, &x, mark, ORC_MVC, 0, RULE_DEG1 | RULE_DEG2TRI);",
+     "        reduce(&g, &x, mark, ORC_MVC, 0, RULE_DEG1);"),
 ]
 
 

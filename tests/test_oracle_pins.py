@@ -70,6 +70,13 @@ def run_pins(orc, quick=False):
         want = (case["expect_deg"], case["expect_S"], case["expect_m"], case["expect_pruned"])
         if got != want:
             fails.append(f"rule case {case['name']}: {got} != {want}")
+    for case in pins.load_greedy_cases():
+        g = G.csr_from_edges(case["n"], [e[0] for e in case["edges"]], [e[1] for e in case["edges"]])
+        size, cover = orc.greedy(g)
+        got = (size, sorted(int(v) for v in np.flatnonzero(cover)))
+        want = (case["expect_greedy"], case["expect_cover"])
+        if got != want:
+            fails.append(f"greedy case {case['name']}: {got} != {want}")
     return fails
 
 
