@@ -34,6 +34,10 @@
  *   R6 PVC answers yes at once, with the greedy cover, when greedy <= k; k < 0 is always no.
  *   R7 Branch vertex: maximum current degree, ties to the lowest id.  The search visits the
  *      "take v" child before the "take N(v)" child.
+ *
+ * Pins (tests/test_oracle_pins.py): closed forms, brute force, Konig, complement cliques, tree
+ * dynamic programme, disjoint unions, PVC around the minimum, hand-derived rule cases and greedy
+ * runs.  Parity unpinned: the node counts and which minimum cover the search returns.
  */
 #include <stdint.h>
 #include <stdlib.h>
