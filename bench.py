@@ -36,6 +36,12 @@ CPU_SAMPLE_GRAPHS = 256  # about 15 s of single-core oracle work
 PLAIN_SAMPLE_GRAPHS = 512
 # Kernels in one replay of the batch plan: worklist init, greedy bound, traversal, answer gather.
 KERNELS_PER_STEP = 4
+# Records one vc_mvc_batch call copies besides the CSR and the covers (sizes of the C structs,
+# checked by tests/test_bench_contract.py): a Problem per graph, the control block, the per-SM
+# node counters.
+PROBLEM_RECORD_BYTES = 128
+CONTROL_BYTES = 1152
+SM_COUNTER_BYTES = 1024 * 8
 
 
 def parse():
@@ -79,6 +85,16 @@ def combine(t_local: float, solves_local: int, device=None):
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     dist.all_reduce(n, op=dist.ReduceOp.SUM)
     return float(t.item()), int(n.item())
+
+
+def e2e_copy_bytes(b, total_n: int) -> tuple[int, int]:
+    """Bytes one vc_mvc_batch call with host buffers copies: up, the packed CSR, the problem table
+    and the expected neighbour-list lengths; down, the problem table, the control block, the
+    per-SM node counters and the cover masks (total_n int32)."""
+    G = len(b.vtx) - 1
+    h2d = int(b.offsets.nbytes + b.neighbors.nbytes) + G * (PROBLEM_RECORD_BYTES + 8)
+    d2h = G * PROBLEM_RECORD_BYTES + CONTROL_BYTES + SM_COUNTER_BYTES + 4 * int(total_n)
+    return h2d, d2h
 
 
 def peaks():
@@ -361,10 +377,7 @@ def run_ours(a):
         sizes_h, covers_h, st_h = vc.mvc_batch(b.vtx, b.edge, off_h.numpy(), nbr_h.numpy(), stream=stream)
         e2e_ms.append(1000 * (time.perf_counter() - t0))
     G = a.graphs
-    # bytes the library copies per call: packed CSR + problem table + expected lengths up; problem
-    # table, control block, per-SM counters and the Σn cover masks down
-    h2d = int(b.offsets.nbytes + b.neighbors.nbytes + G * 64 + G * 8)
-    d2h = int(G * 64 + 128 + 1024 * 8 + total_n * 4)
+    h2d, d2h = e2e_copy_bytes(b, total_n)
     e2e_value = solves / world / (sum(e2e_ms) / 1000.0) * world if e2e_ms else None
 
     out = None

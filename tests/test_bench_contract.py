@@ -54,3 +54,26 @@ def test_source_hash_follows_code_not_comments(tmp_path):
     assert anchor in text
     dev.write_text(text.replace(anchor, "constexpr unsigned kFull = 0x7fffffffu;"))
     assert bench.traversal_source_hash(str(copy)) != base
+
+
+def test_e2e_copy_bytes_follow_the_c_structs(tmp_path):
+    # The e2e line's byte counts use the sizes of the records the library really copies: pinned
+    # here to the C structs by compiling their sizes out of the library's own header.
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2204_10402_gb300 import graphs as G
+    src = tmp_path / "sizes.cpp"
+    src.write_text('#include <cstdio>\n#include "vc_internal.h"\n'
+                   'int main() { std::printf("%zu %zu %d\\n", sizeof(vc::Problem), sizeof(vc::Control), '
+                   '(int)vc::kSmSlots); }\n')
+    exe = tmp_path / "sizes"
+    csrc = os.path.join(ROOT, "paper_2204_10402_gb300", "csrc")
+    r = subprocess.run(["g++", "-std=c++17", "-I", csrc, "-o", str(exe), str(src)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    prob, ctrl, slots = map(int, subprocess.run([str(exe)], capture_output=True, text=True).stdout.split())
+    assert (bench.PROBLEM_RECORD_BYTES, bench.CONTROL_BYTES, bench.SM_COUNTER_BYTES) == (prob, ctrl, 8 * slots)
+    b = G.pack([G.path(3), G.petersen()])          # offsets 4 + 11 entries, neighbours 4 + 30
+    h2d, d2h = bench.e2e_copy_bytes(b, 13)
+    assert h2d == 4 * (15 + 34) + 2 * (prob + 8)
+    assert d2h == 2 * prob + ctrl + 8 * slots + 4 * 13
+    assert isinstance(h2d, int) and isinstance(d2h, int)
