@@ -93,6 +93,7 @@ class ServerCounters(ctypes.Structure):
 
 
 _lib = None
+_lib_path = None
 
 
 def library_path() -> str:
@@ -100,9 +101,13 @@ def library_path() -> str:
 
 
 def load(path: str | None = None):
-    """Loads libvc.so (raising if it is missing) and declares the C signatures."""
-    global _lib
+    """Loads libvc.so (raising if it is missing) and declares the C signatures.  ``path`` selects
+    another build of the library (an instrumented variant, see build.build_variant); a process
+    loads one library only."""
+    global _lib, _lib_path
     if _lib is not None:
+        if path is not None and os.path.abspath(path) != _lib_path:
+            raise RuntimeError(f"{_lib_path} is already loaded in this process; cannot also load {path}")
         return _lib
     path = path or LIB_PATH
     if not os.path.exists(path):
@@ -140,6 +145,7 @@ def load(path: str | None = None):
                  "vc_plan_create_mvc_batch", "vc_plan_launch", "vc_plan_results", "vc_plan_destroy"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
+    _lib_path = os.path.abspath(path)
     return lib
 
 
