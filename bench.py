@@ -107,8 +107,8 @@ def peaks():
 
 
 # The files that define the profiled traversal kernel (its code, layout and launch).
-TRAVERSAL_SOURCES = ("vc_internal.h", "vc_device.cuh", "vc_kernels.cuh", "vc_launch.h", "vc_launch_impl.cuh",
-                     "vc_kern_w16_rows.cu", "vc_kern_w32_rows.cu")
+TRAVERSAL_SOURCES = ("vc_internal.h", "vc_device.cuh", "vc_rows.cuh", "vc_kernels.cuh", "vc_launch.h",
+                     "vc_launch_impl.cuh", "vc_kern_w16_rows.cu", "vc_kern_w32_rows.cu")
 
 
 def code_only(text: str) -> str:

@@ -1,6 +1,8 @@
-// vc_device.cuh - device building blocks of the traversal: one worker (a thread block of WT
-// threads) holds the current tree node in shared memory and applies the reduction rules, the
-// maximum-degree selection and the two branch removals to it.
+// vc_device.cuh - device building blocks of the traversal: the CSR-walk worker (a thread block
+// of WT threads) holds the current tree node in shared memory and applies the reduction rules,
+// the maximum-degree selection and the two branch removals to it by walking the CSR.  (Graphs of
+// at most 256 vertices may use the bit-row worker of vc_rows.cuh instead, which has the same
+// interface.)
 //
 // Shared-memory layout of a worker (all offsets 16-byte aligned):
 //   [entry]  EntryHeader (16 B) + degree array W[n_max] padded to 16 B   <- copied to/from stacks
@@ -12,9 +14,6 @@
 //   [sc]     kScratchWords int32: tallies, broadcasts, per-warp reduction keys, trace slots
 //   [csr]    optional copy of the current graph's CSR (offsets, then neighbours), so that the
 //            adjacency walks of the rules and branches cost shared-memory latency
-//   [rows]   bit-row workers (NW > 0) only: the live-vertex mask and the pass's chosen set
-//            (max(NW, 4) words each), then the current graph's adjacency as one NW-word bit row
-//            per vertex (a read-only copy of the CSR, like [csr])
 // The global-memory version (GM) keeps [entry]'s degree array, [marks], [dirty] and [list] in a
 // per-worker global region instead; the header and [sc] stay in shared memory.
 //
@@ -297,19 +296,16 @@ template <> struct RowVec<8> {
 // removal list live in a global-memory region of this worker (the header and scratch stay in
 // shared memory); their reads go through L2 (.cg) because the atomics that change them act there.
 //
-// NW > 0 (one-warp workers, graphs of at most 32*NW vertices): bit-row worker.  The node is the
-// same degree array, but the rules find neighbours, test adjacency and apply removals through
-// bit rows of the adjacency matrix instead of walking the CSR: a degree-one vertex's neighbour is
-// the lowest bit of row(v) & live; a removal recomputes each live vertex's degree as
-// popc(row(v) & live') lane-parallel, with no atomics.  The rounds, tie-breaks and resulting
-// degree arrays are the same as the CSR walks'.
-template <typename W, int WT, bool GM = false, int NW = 0>
+// The kernels use a worker through this interface (shared with RowWorker, vc_rows.cuh): node
+// accessors (node_S, node_m, node_branch, node_problem), loading and storing (load_root,
+// load_entry, node_loaded, store_entry, load_plain, save_plain), the rule passes, apply,
+// size_exceeded and must_stop, argmax, the two branches (take_vertex, take_neighbourhood) and
+// write_cover.
+template <typename W, int WT, bool GM = false>
 struct Worker {
-    static_assert(NW == 0 || NW == 1 || NW == 2 || NW == 4 || NW == 8, "bit rows of 1, 2, 4 or 8 words");
-    static_assert(NW == 0 || (WT == 32 && !GM), "bit rows are for one-warp shared-memory workers");
+    static constexpr int kWT = WT;
     static constexpr int kWarps = WT / 32;
-    static constexpr int kNW = NW > 0 ? NW : 1;  // array extent for the bit-row helpers
-    static constexpr int kMaskWords = kNW > 4 ? kNW : 4;  // live / chosen masks, 16-byte multiples
+    static constexpr int kRowWords = 0;  // no bit rows
     EntryHeader *hdr;
     W *d;
     uint32_t *marks;
@@ -319,9 +315,6 @@ struct Worker {
     unsigned long long *keys;
     unsigned long long *tally;
     int32_t *csr;
-    uint32_t *livew;  // bit-row workers: live-vertex mask (NW words)
-    uint32_t *newm;   // bit-row workers: vertices chosen for S in the current pass (NW words)
-    uint32_t *rows;   // bit-row workers: adjacency bit rows, NW words per vertex
     int tid, lane, warp;
     int32_t entry_bytes;
     int32_t csr_words;
@@ -344,12 +337,6 @@ struct Worker {
             dirty = reinterpret_cast<unsigned long long *>(g + mark_bytes);
             list = reinterpret_cast<int32_t *>(g + mark_bytes + dirty_bytes);
             sc = reinterpret_cast<int32_t *>(smem + 16);
-        } else if constexpr (NW > 0) {  // bit-row workers need no marks or removal list
-            d = reinterpret_cast<W *>(smem + 16);
-            marks = nullptr;
-            list = nullptr;
-            dirty = reinterpret_cast<unsigned long long *>(smem + eb);
-            sc = reinterpret_cast<int32_t *>(smem + eb + dirty_bytes);
         } else {
             d = reinterpret_cast<W *>(smem + 16);
             marks = reinterpret_cast<uint32_t *>(smem + eb);
@@ -361,9 +348,6 @@ struct Worker {
         tally = reinterpret_cast<unsigned long long *>(sc + kScTally);
         csr = sc + kScratchWords;
         csr_words = csr_capacity;
-        livew = reinterpret_cast<uint32_t *>(csr) + pad16((int64_t)csr_capacity * 4) / 4;
-        newm = livew + kMaskWords;
-        rows = livew + 2 * kMaskWords;
         staged = -1;
         staged_full = false;
         dbg = nullptr;
@@ -443,12 +427,6 @@ struct Worker {
     __device__ __forceinline__ void touch(int x, int nd) {
         if (nd == 1 || nd == 2) atomicOr(&dirty[x >> 5], (nd == 1 ? 1ull : 0x100000000ull) << (x & 31));
     }
-    // Dirty words for the 32 vertices of a chunk from the lanes' new degrees (changed lanes only).
-    static __device__ __forceinline__ unsigned long long dirty_bits(bool changed, int nd) {
-        const unsigned b1 = __ballot_sync(kFull, changed && nd == 1);
-        const unsigned b2 = __ballot_sync(kFull, changed && nd == 2);
-        return (unsigned long long)b1 | ((unsigned long long)b2 << 32);
-    }
     __device__ void dirty_all(int n) {
         for (int i = tid; i < (n + 31) / 32; i += WT) {
             const int rem = n - 32 * i;
@@ -463,25 +441,21 @@ struct Worker {
     // Clears scratch state; call once per kernel before any pass.
     __device__ void init_scratch(int32_t n_max) {
         for (int i = tid; i < (n_max + 31) / 32; i += WT) {
-            if constexpr (NW == 0) marks[i] = 0;  // bit-row workers have no marks
+            marks[i] = 0;
             dirty[i] = 0ull;
         }
         for (int i = tid; i < kScratchWords; i += WT) sc[i] = (i == kScMaxDeg) ? INT32_MAX : 0;
-        if constexpr (NW > 0)
-            for (int i = tid; i < 2 * kMaskWords; i += WT) livew[i] = 0u;  // live and chosen masks
         sync();
     }
 
     // Points c at a shared-memory copy of its graph's offsets -- and of its neighbour lists too
-    // when the launch reserved room for them -- copied when the problem changes.  Bit-row
-    // workers also load the graph's bit rows: BUILD = true builds them from the CSR (and writes
-    // them to `grows` when it is given); BUILD = false copies them from `grows`, where the
-    // greedy pass left them (the traversal, which then carries no build code).
+    // when the launch reserved room for them -- copied when the problem changes.  (BUILD and
+    // grows concern bit-row workers only.)
     template <bool BUILD = true>
-    __device__ void stage(Ctx &c, uint32_t *grows = nullptr) {
+    __device__ void stage(Ctx &c, uint32_t * = nullptr) {
         const int n1 = c.n + 1;
         const bool copy_csr = csr_words > 0 && n1 <= csr_words;
-        if (NW == 0 && !copy_csr) return;  // nothing to stage: read global memory
+        if (!copy_csr) return;  // nothing to stage: read global memory
         if (c.index == staged) {
             if (copy_csr) {
                 c.off = csr;
@@ -498,7 +472,6 @@ struct Worker {
             if (full)
                 for (int i = tid; i < len; i += WT) csr[n1 + i] = c.adj[i];
         }
-        if constexpr (NW > 0) stage_rows<BUILD>(c, grows);
         staged = c.index;
         staged_full = full;
         sync();
@@ -506,71 +479,6 @@ struct Worker {
             c.off = csr;
             if (full) c.adj = csr + n1;
         }
-    }
-
-    // Bit rows of the graph (lane-parallel: lane handles vertices lane, lane+32, ...).
-    template <bool BUILD>
-    __device__ void stage_rows(const Ctx &c, uint32_t *grows) {
-        using V = typename RowVec<kNW>::type;
-        V *r = reinterpret_cast<V *>(rows);
-        if constexpr (!BUILD) {
-            if (!grows) {  // the host always gives bit-row traversals their rows
-                if (lane == 0 && dbg) raise_status(dbg, VC_EINVAL);
-                for (int v = lane; v < c.n; v += 32) r[v] = V{};  // empty rows until the launch stops
-                return;
-            }
-            const V *g = reinterpret_cast<const V *>(grows);
-            for (int v = lane; v < c.n; v += 32) r[v] = RowVec<kNW>::load_cg(g + v);
-        } else {
-            for (int v = lane; v < c.n; v += 32) {
-                uint32_t b[kNW];
-#pragma unroll
-                for (int w = 0; w < NW; ++w) b[w] = 0u;
-                const int lo = c.off[v], hi = c.off[v + 1];
-                for (int j = lo; j < hi; ++j) {
-                    const int x = c.adj[j];
-                    VC_CHECK(dbg, x >= 0 && x < 32 * NW, 21, x, continue);
-#pragma unroll
-                    for (int w = 0; w < NW; ++w) b[w] |= ((x >> 5) == w) ? (1u << (x & 31)) : 0u;
-                }
-                const V q = RowVec<kNW>::pack(b);
-                r[v] = q;
-                if (grows) RowVec<kNW>::store_cg(reinterpret_cast<V *>(grows) + v, q);
-            }
-        }
-    }
-
-    // ---- bit-row helpers (NW > 0) --------------------------------------------------------------
-
-    __device__ __forceinline__ void row(int v, uint32_t (&b)[kNW]) const {
-        RowVec<kNW>::unpack(reinterpret_cast<const typename RowVec<kNW>::type *>(rows)[v], b);
-    }
-    __device__ __forceinline__ void live_words(uint32_t (&b)[kNW]) const {
-        RowVec<kNW>::unpack(*reinterpret_cast<const typename RowVec<kNW>::type *>(livew), b);
-    }
-    __device__ __forceinline__ void chosen_words(uint32_t (&b)[kNW]) const {
-        RowVec<kNW>::unpack(*reinterpret_cast<const typename RowVec<kNW>::type *>(newm), b);
-    }
-    __device__ __forceinline__ bool row_has(int u, int x) const { return (rows[u * NW + (x >> 5)] >> (x & 31)) & 1u; }
-
-    // Live mask of the current node from its degree array (after a node is loaded).
-    // (Also the bound on the largest live degree that lets high-degree passes be skipped.)
-    __device__ void init_live(const Ctx &c) {
-        int mx = 0;
-#pragma unroll 1
-        for (int k = 0; k < NW; ++k) {
-            const int v = 32 * k + lane;
-            const int dv = v < c.n ? deg(v) : -1;
-            const unsigned m = __ballot_sync(kFull, dv != -1);
-            mx = max(mx, dv);
-            if (lane == 0) {
-                livew[k] = m;
-                newm[k] = 0u;
-            }
-        }
-        mx = (int)__reduce_max_sync(kFull, (unsigned)max(mx, 0));
-        if (lane == 0) sc[kScMaxDeg] = mx;
-        __syncwarp();
     }
 
     // ---- node loading / storing ---------------------------------------------------------------
@@ -589,7 +497,6 @@ struct Worker {
             hdr->branch = -1;
         }
         sync();
-        if constexpr (NW > 0) init_live(c);
     }
 
     // Copies an entry of `bytes` (header + degree array of the entry's graph) from global memory.
@@ -674,204 +581,6 @@ struct Worker {
         sync();
     }
 
-    // ---- bit-row removal and rules (NW > 0) -------------------------------------------------------
-
-    // Moves the chosen set newm into S.  One chosen vertex u (the "v" child and most single rule
-    // removals): u's live neighbours lose one degree each and m loses deg(u).  Several: every live
-    // vertex outside the set gets its degree recomputed as popc(row & live'), and m = (sum of live
-    // degrees) / 2.  Either way a vertex whose degree changed to one or two is marked dirty for the
-    // pass that degree concerns, and the result equals apply_list's decrements.  (The
-    // single-vertex loop over 32-vertex chunks stays rolled and the general one is unrolled: each
-    // measured fastest, the traversal being sensitive to its code size.)
-    __device__ void apply_rows(const Ctx &c) {
-        __syncwarp();  // every proposal (shared atomics) is done
-        uint32_t nl[kNW];
-        live_words(nl);
-        int cnt = 0, u = -1;
-#pragma unroll
-        for (int w = 0; w < NW; ++w) {
-            const uint32_t rw = newm[w];
-            nl[w] &= ~rw;
-            cnt += __popc(rw);
-            if (u < 0 && rw) u = 32 * w + __ffs(rw) - 1;
-        }
-        const int chunks = (c.n + 31) >> 5;
-        if (cnt == 1) {
-            // One vertex u (the "v" child, most single rule removals): its live neighbours lose
-            // one degree each and are exactly the vertices whose degree changes; m loses deg(u).
-            const int du = deg(u);
-            const uint32_t *ru = rows + u * NW;
-#pragma unroll 1
-            for (int k = 0; k < chunks; ++k) {
-                const uint32_t hit = ru[k] & livew[k];  // u itself has no self-loop bit
-                if (hit == 0u) continue;
-                const int v = 32 * k + lane;
-                const bool mine = (hit >> lane) & 1u;
-                const int nd = mine ? deg(v) - 1 : 0;
-                if (mine) d[v] = (W)nd;
-                const unsigned long long db = dirty_bits(mine, nd);
-                if (lane == 0 && db) dirty[k] |= db;
-            }
-            if (lane == 0) {
-                d[u] = (W)-1;
-                hdr->S += 1;
-                hdr->m -= du;
-                tally[kTCsr] += (unsigned long long)(c.off[u + 1] - c.off[u]);
-            }
-        } else {
-            int degsum = 0, words = 0, maxd = 0;
-#pragma unroll
-            for (int k = 0; k < NW; ++k) {
-                if (k >= chunks) break;
-                const int v = 32 * k + lane;
-                bool changed = false;
-                int nd = -1;
-                if (v < c.n) {
-                    const int dv = deg(v);
-                    if ((newm[k] >> lane) & 1u) {
-                        d[v] = (W)-1;
-                        words += c.off[v + 1] - c.off[v];
-                    } else if (dv >= 0) {
-                        uint32_t b[kNW];
-                        row(v, b);
-                        nd = 0;
-#pragma unroll
-                        for (int w = 0; w < NW; ++w) nd += __popc(b[w] & nl[w]);
-                        if (nd != dv) {
-                            d[v] = (W)nd;
-                            changed = true;
-                        }
-                        degsum += nd;
-                        maxd = max(maxd, nd);
-                    }
-                }
-                const unsigned long long db = dirty_bits(changed, nd);
-                if (lane == 0 && db) dirty[k] |= db;
-            }
-            degsum = __reduce_add_sync(kFull, degsum);
-            words = __reduce_add_sync(kFull, words);
-            const int mx = (int)__reduce_max_sync(kFull, (unsigned)maxd);
-            if (lane == 0) {
-                hdr->S += cnt;
-                hdr->m = degsum / 2;
-                sc[kScMaxDeg] = mx;
-                tally[kTCsr] += (unsigned long long)words;
-            }
-        }
-        __syncwarp();  // every lane has read newm and livew
-        if (lane == 0) {
-            using V = typename RowVec<kNW>::type;
-            *reinterpret_cast<V *>(livew) = RowVec<kNW>::pack(nl);
-            *reinterpret_cast<V *>(newm) = V{};
-        }
-        __syncwarp();
-    }
-
-    // Ends a bit-row scan: returns whether any lane chose a vertex (the choice waits in newm).
-    // (Bit-row scans walk no CSR; csr_words counts the removals' adjacency lists, the part of the
-    // algorithmic traffic that every implementation reads.)
-    __device__ __forceinline__ bool rows_finish(bool proposed, int slot, long long t0) {
-        if (lane == 0) tally[kTPasses] += 1;
-        const bool any = __any_sync(kFull, proposed);
-        VC_CYC_ADD(*this, slot, t0);
-        VC_CYC_INC(*this, slot + (kPDeg1Count - kPDeg1));
-        return any;
-    }
-
-    // Degree-one over bit rows: a dirty degree-one vertex's neighbour is the lowest bit of
-    // row(v) & live (one lane per vertex; same tie-break as pass_degree_one).
-    __device__ bool rows_pass_degree_one(const Ctx &c) {
-        const long long t0 = VC_CYC();
-        bool proposed = false;
-        const int chunks = (c.n + 31) >> 5;
-#pragma unroll
-        for (int k = 0; k < NW; ++k) {
-            if (k >= chunks) break;
-            const unsigned long long dw = dirty[k];
-            const unsigned bits = (unsigned)dw;
-            if (bits == 0u) continue;
-            if (lane == 0) dirty[k] = dw & 0xffffffff00000000ull;
-            const int v = 32 * k + lane;
-            if (((bits >> lane) & 1u) && v < c.n && deg(v) == 1) {
-                uint32_t b[kNW], lv[kNW];
-                row(v, b);
-                live_words(lv);
-                // deg(v) = 1: exactly one bit is set
-                int u = -1;
-#pragma unroll
-                for (int w = 0; w < NW; ++w) {
-                    const uint32_t m = b[w] & lv[w];
-                    if (m) u = 32 * w + __ffs(m) - 1;
-                }
-                if (u >= 0 && !(deg(u) == 1 && u > v)) {
-                    atomicOr(&newm[u >> 5], 1u << (u & 31));
-                    proposed = true;
-                }
-            }
-        }
-        return rows_finish(proposed, kPDeg1, t0);
-    }
-
-    // Degree-two-triangle over bit rows: the two lowest bits of row(v) & live are u < w, and uw is
-    // an edge iff bit w of row(u) is set (same tie-break as pass_degree_two_triangle).
-    __device__ bool rows_pass_degree_two_triangle(const Ctx &c) {
-        const long long t0 = VC_CYC();
-        bool proposed = false;
-        const int chunks = (c.n + 31) >> 5;
-#pragma unroll
-        for (int k = 0; k < NW; ++k) {
-            if (k >= chunks) break;
-            const unsigned long long dw = dirty[k];
-            const unsigned bits = (unsigned)(dw >> 32);
-            if (bits == 0u) continue;
-            if (lane == 0) dirty[k] = dw & 0xffffffffull;
-            const int v = 32 * k + lane;
-            if (((bits >> lane) & 1u) && v < c.n && deg(v) == 2) {
-                uint32_t b[kNW], lv[kNW];
-                row(v, b);
-                live_words(lv);
-#pragma unroll
-                for (int w = 0; w < NW; ++w) b[w] &= lv[w];
-                // deg(v) = 2: exactly two bits are set; u is the lowest, x the highest
-                int u = -1, x = -1;
-#pragma unroll
-                for (int w = 0; w < NW; ++w) {
-                    if (b[w]) {
-                        if (u < 0) u = 32 * w + __ffs(b[w]) - 1;
-                        x = 32 * w + 31 - __clz(b[w]);
-                    }
-                }
-                if (u >= 0 && x > u && row_has(u, x) && !((deg(u) == 2 && u < v) || (deg(x) == 2 && x < v))) {
-                    atomicOr(&newm[u >> 5], 1u << (u & 31));
-                    atomicOr(&newm[x >> 5], 1u << (x & 31));
-                    proposed = true;
-                }
-            }
-        }
-        return rows_finish(proposed, kPTri, t0);
-    }
-
-    // High-degree over the lanes' own vertices: one ballot per 32 vertices.
-    // Skipped (finds nothing, scans nothing) while the largest live degree cannot exceed the
-    // threshold: degrees only fall within a node, so the bound from the last recount holds.
-    __device__ bool rows_pass_high_degree(const Ctx &c, int32_t bound) {
-        const long long t0 = VC_CYC();
-        const int thr = (c.kind == kMVC) ? bound - hdr->S - 1 : bound - hdr->S;
-        if (sc[kScMaxDeg] <= thr) return false;
-        bool proposed = false;
-        const int chunks = (c.n + 31) >> 5;
-#pragma unroll
-        for (int k = 0; k < NW; ++k) {
-            if (k >= chunks) break;
-            const int v = 32 * k + lane;
-            const int dv = v < c.n ? deg(v) : -1;
-            const unsigned m = __ballot_sync(kFull, dv != -1 && dv > thr);
-            if (lane == 0) newm[k] = m;
-            proposed |= m != 0u;
-        }
-        return rows_finish(proposed, kPHigh, t0);
-    }
-
     // Ends a scan: returns whether some thread proposed a vertex (the proposals wait in the
     // removal list).  (slot, t0: VC_TRACE accounting of the scan.)
     __device__ __forceinline__ bool finish_pass(bool proposed, int slot, long long t0) {
@@ -884,39 +593,20 @@ struct Worker {
 
     // Whether a branch left a removal waiting (uniform; take_vertex / take_neighbourhood end with
     // a barrier).
-    __device__ __forceinline__ bool has_pending() const {
-        if constexpr (NW > 0) {
-            uint32_t b[kNW];
-            chosen_words(b);
-            bool any = false;
-#pragma unroll
-            for (int w = 0; w < NW; ++w) any |= b[w] != 0u;
-            return any;
-        } else {
-            return sc[kScCount] != 0;
-        }
-    }
+    __device__ __forceinline__ bool has_pending() const { return sc[kScCount] != 0; }
 
     // Drops a pending removal (a node abandoned before its reduction).
     __device__ void discard_pending() {
-        if constexpr (NW > 0) {
-            if (lane == 0) {
-#pragma unroll
-                for (int w = 0; w < NW; ++w) newm[w] = 0u;
-            }
-        } else {
-            const int cnt = sc[kScCount];
-            for (int i = tid; i < cnt; i += WT) marks[ld_list(i) >> 5] = 0u;
-            sync();
-            if (tid == 0) sc[kScCount] = 0;
-        }
+        const int cnt = sc[kScCount];
+        for (int i = tid; i < cnt; i += WT) marks[ld_list(i) >> 5] = 0u;
+        sync();
+        if (tid == 0) sc[kScCount] = 0;
         sync();
     }
 
     __device__ __forceinline__ void apply(const Ctx &c) {
         const long long t1 = VC_CYC();
-        if constexpr (NW > 0) apply_rows(c);
-        else apply_list(c);
+        apply_list(c);
         VC_CYC_ADD(*this, kPApply, t1);
     }
 
@@ -981,7 +671,6 @@ struct Worker {
     // Degree-one: the live neighbour u of a degree-one vertex v enters S; if u also has degree one
     // (an isolated edge) only the smaller id of the pair enters.
     __device__ bool pass_degree_one(const Ctx &c) {
-        if constexpr (NW > 0) return rows_pass_degree_one(c);
         const long long t0 = VC_CYC();
         bool proposed = false;
         int words = 0;
@@ -1012,7 +701,6 @@ struct Worker {
     // Degree-two-triangle: if N(v) = {u, w} and uw is an edge, u and w enter S; among degree-two
     // vertices of one triangle only the smallest id applies the rule.
     __device__ bool pass_degree_two_triangle(const Ctx &c) {
-        if constexpr (NW > 0) return rows_pass_degree_two_triangle(c);
         const long long t0 = VC_CYC();
         bool proposed = false;
         int words = 0;
@@ -1050,7 +738,6 @@ struct Worker {
     // runs leaves as the new bound the largest degree it did not choose (the chosen vertices
     // leave the graph and the rest only lose degree).
     __device__ bool pass_high_degree(const Ctx &c, int32_t bound) {
-        if constexpr (NW > 0) return rows_pass_high_degree(c, bound);
         const long long t0 = VC_CYC();
         const int thr = (c.kind == kMVC) ? bound - hdr->S - 1 : bound - hdr->S;
         if (sc[kScMaxDeg] <= thr) return false;
@@ -1080,40 +767,6 @@ struct Worker {
         return (c.kind == kMVC) ? hdr->S >= bound : hdr->S > bound;
     }
 
-    // Applies a pending branch removal, then the chosen rules in the order degree-one,
-    // degree-two-triangle, high-degree, cyclically, until every chosen rule in a row has found
-    // nothing.  This is the fixpoint of repeating whole rounds until a round changes nothing: a
-    // rule that found nothing in a state finds nothing in it again, so the passes a round-based
-    // loop would add after that point cannot change the state.  With early_exit, returns true as
-    // soon as |S| alone prunes the node (sound: |S| only grows).  The removal is applied at this
-    // one place, which keeps the kernel's code small.
-    __device__ bool reduce(const Ctx &c, int32_t bound, int rules, bool early_exit) {
-        const int nrules = __popc(rules & kRuleAll);
-        int quiet = 0, r = 0;
-        bool pend = has_pending();
-        if (early_exit && size_exceeded(c, bound)) {  // best fell since the node was made
-            if (pend) discard_pending();
-            return true;
-        }
-        for (;;) {
-            if (pend) {
-                apply(c);
-                quiet = 0;
-                if (early_exit && size_exceeded(c, bound)) return true;
-            }
-            if (quiet >= nrules) return false;
-            const bool on = (rules >> r) & 1;
-            pend = false;
-            if (on) {
-                if (r == 0) pend = pass_degree_one(c);
-                else if (r == 1) pend = pass_degree_two_triangle(c);
-                else pend = pass_high_degree(c, bound);
-                if (!pend) ++quiet;
-            }
-            r = (r == 2) ? 0 : r + 1;
-        }
-    }
-
     // Stop check (Sec. II-B): prune when |S| is too large or m > t^2 with t = best-|S|-1 (MVC) or
     // k-|S| (PVC).
     __device__ __forceinline__ bool must_stop(const Ctx &c, int32_t bound) const {
@@ -1122,9 +775,9 @@ struct Worker {
         return (long long)hdr->m > t * t;
     }
 
-    // Maximum-degree live vertex, lowest id on ties (Sec. II-B, IV-B).  Key = (d+1, ~v) so removed
-    // vertices (key 0) never win; returns -1 when no vertex is live.
-    __device__ int argmax(const Ctx &c) {
+    // Maximum-degree live vertex, lowest id on ties (Sec. II-B, IV-B), and its degree dv.
+    // Key = (d+1, ~v) so removed vertices (key 0) never win; returns -1 when no vertex is live.
+    __device__ int argmax(const Ctx &c, int &dv) {
         unsigned long long key = 0ull;
         for (int v = tid; v < c.n; v += WT) {
             const int dv = deg(v);
@@ -1140,6 +793,7 @@ struct Worker {
             unsigned long long k2 = lane < kWarps ? keys[lane] : 0ull;
             key = warp_max_u64(k2);
         }
+        dv = (int)(key >> 32) - 1;
         return key == 0ull ? -1 : (int)(0xffffffffu - (uint32_t)key);
     }
 
@@ -1147,11 +801,6 @@ struct Worker {
     // and applied by the next reduce().
     __device__ void take_vertex(const Ctx &c, int v) {
         VC_CHECK(dbg, v >= 0 && v < c.n, 5, v, return);
-        if constexpr (NW > 0) {
-            if (lane == 0) newm[v >> 5] = 1u << (v & 31);  // newm is empty between passes
-            __syncwarp();
-            return;
-        }
         if (tid == 0) propose(v);
         sync();
     }
@@ -1160,20 +809,6 @@ struct Worker {
     // pending and applied by the next reduce().
     __device__ void take_neighbourhood(const Ctx &c, int v) {
         VC_CHECK(dbg, v >= 0 && v < c.n, 6, v, return);
-        if constexpr (NW > 0) {
-            uint32_t b[kNW], lv[kNW];
-            row(v, b);
-            live_words(lv);
-#pragma unroll
-            for (int w = 0; w < NW; ++w) b[w] &= lv[w];
-            if (lane == 0) {
-#pragma unroll
-                for (int w = 0; w < NW; ++w) newm[w] = b[w];
-                tally[kTCsr] += (unsigned long long)(c.off[v + 1] - c.off[v]);
-            }
-            __syncwarp();
-            return;
-        }
         const int lo = c.off[v], hi = c.off[v + 1];
         for (int j = lo + tid; j < hi; j += WT) {
             const int x = c.adj[j];
@@ -1183,10 +818,76 @@ struct Worker {
         sync();
     }
 
+    // Node accessors (the header lives in shared memory; uniform after the worker's barriers).
+    __device__ __forceinline__ int32_t node_S() const { return hdr->S; }
+    __device__ __forceinline__ int32_t node_m() const { return hdr->m; }
+    __device__ __forceinline__ int32_t node_branch() const { return hdr->branch; }
+    __device__ __forceinline__ int32_t node_problem() const { return hdr->problem; }
+    __device__ __forceinline__ void clear_branch() {
+        if (tid == 0) hdr->branch = -1;
+    }
+    __device__ __forceinline__ void node_loaded(const Ctx &) {}  // the node is complete as loaded
+    __device__ __forceinline__ void flush_counts() {}            // statistics live in shared memory
+
+    // A degree array given from outside (rule tests): every vertex dirty unless the state is a
+    // fixpoint that a branch is about to change.
+    __device__ void load_plain(const Ctx &c, const int32_t *deg_in, int32_t S0, int32_t m0, bool all_dirty) {
+        for (int v = tid; v < c.n; v += WT) {
+            if constexpr (GM) __stcg(d + v, (W)deg_in[v]);
+            else d[v] = (W)deg_in[v];
+        }
+        if (all_dirty) dirty_all(c.n);
+        if (tid == 0) {
+            hdr->problem = c.index;
+            hdr->S = S0;
+            hdr->m = m0;
+            hdr->branch = -1;
+        }
+        sync();
+    }
+    __device__ void save_plain(const Ctx &c, int32_t *deg_out) const {
+        for (int v = tid; v < c.n; v += WT) deg_out[v] = deg(v);
+    }
+
     // Writes the current node's S as a 0/1 mask.
     __device__ void write_cover(const Ctx &c) {
         for (int v = tid; v < c.n; v += WT) __stcg(c.cover + v, deg(v) == -1 ? 1 : 0);
     }
 };
+
+// Applies a pending branch removal, then the chosen rules in the order degree-one,
+// degree-two-triangle, high-degree, cyclically, until every chosen rule in a row has found
+// nothing.  This is the fixpoint of repeating whole rounds until a round changes nothing: a rule
+// that found nothing in a state finds nothing in it again, so the passes a round-based loop would
+// add after that point cannot change the state.  With early_exit, returns true as soon as |S|
+// alone prunes the node (sound: |S| only grows).  The removal is applied at this one place, which
+// keeps the kernel's code small.  (Any worker type: Worker or RowWorker.)
+template <class Wk>
+__device__ bool reduce_fixpoint(Wk &w, const Ctx &c, int32_t bound, int rules, bool early_exit) {
+    const int nrules = __popc(rules & kRuleAll);
+    int quiet = 0, r = 0;
+    bool pend = w.has_pending();
+    if (early_exit && w.size_exceeded(c, bound)) {  // best fell since the node was made
+        if (pend) w.discard_pending();
+        return true;
+    }
+    for (;;) {
+        if (pend) {
+            w.apply(c);
+            quiet = 0;
+            if (early_exit && w.size_exceeded(c, bound)) return true;
+        }
+        if (quiet >= nrules) return false;
+        const bool on = (rules >> r) & 1;
+        pend = false;
+        if (on) {
+            if (r == 0) pend = w.pass_degree_one(c);
+            else if (r == 1) pend = w.pass_degree_two_triangle(c);
+            else pend = w.pass_high_degree(c, bound);
+            if (!pend) ++quiet;
+        }
+        r = (r == 2) ? 0 : r + 1;
+    }
+}
 
 }  // namespace vc

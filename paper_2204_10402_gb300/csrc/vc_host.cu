@@ -375,7 +375,7 @@ int run(Workspace &ws, const Spec &spec, const vc_config *cfg_in, cudaStream_t s
     res.workers = workers;
     res.wt = wt;
     res.width = width;
-    res.csr_staged = csr_words > 0;
+    res.csr_staged = nw == 0 && csr_words > 0;  // bit-row workers stage no CSR
     res.gm = gm;
     res.nw = nw;
     res.eb = eb;

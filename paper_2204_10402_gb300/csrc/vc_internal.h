@@ -149,19 +149,16 @@ VC_HD inline int32_t entry_bytes_for(int32_t n_max, int32_t width_bytes) {
 constexpr int kScratchWords = 112;
 // Per-SM node counters are indexed by %smid modulo this power of two.
 constexpr int kSmSlots = 1024;
+// Bit-row workers (nw > 0 words per row) hold the node in registers and keep only the scratch
+// words, each vertex's input degree (a byte) and the bit rows; they stage no CSR.
 VC_HD inline int32_t smem_bytes_for(int32_t n_max, int32_t width_bytes, int32_t csr_words = 0, int32_t nw = 0) {
+    if (nw > 0) return kScratchWords * 4 + pad16(n_max) + pad16((int64_t)n_max * nw * 4);
     int64_t b = entry_bytes_for(n_max, width_bytes);
-    if (nw == 0) {
-        b += pad16(((int64_t)n_max + 31) / 32 * 4);  // marks
-        b += pad16((int64_t)n_max * 4);             // removal list
-    }
+    b += pad16(((int64_t)n_max + 31) / 32 * 4);  // marks
+    b += pad16((int64_t)n_max * 4);             // removal list
     b += pad16(((int64_t)n_max + 31) / 32 * 8);  // dirty bits (two per vertex)
     b += kScratchWords * 4;
     b += pad16((int64_t)csr_words * 4);         // staged CSR
-    if (nw > 0) {                                // bit-row workers: live and chosen masks, rows
-        const int64_t mask_bytes = (nw > 4 ? nw : 4) * 4;
-        b += 2 * mask_bytes + pad16((int64_t)n_max * nw * 4);
-    }
     return (int32_t)b;
 }
 

@@ -13,8 +13,21 @@
 #pragma once
 
 #include "vc_device.cuh"
+#include "vc_rows.cuh"
 
 namespace vc {
+
+// The worker a kernel instance uses: bit rows (NW > 0: one-warp RowWorker, node in registers) or
+// CSR walks (Worker of WT threads, node in shared or, GM, global memory).
+template <typename W, int WT, bool GM, int NW, bool ROWS = (NW > 0)>
+struct WorkerSel {
+    using type = Worker<W, WT, GM>;
+};
+template <typename W, int WT, bool GM, int NW>
+struct WorkerSel<W, WT, GM, NW, true> {
+    static_assert(WT == 32 && !GM, "bit rows are for one-warp shared-memory workers");
+    using type = RowWorker<W, NW>;
+};
 
 // ------------------------------------------------------------------------------------------------
 // CSR validation: offsets monotone from 0, neighbours in range, sorted strictly ascending, no
@@ -41,8 +54,8 @@ __device__ __forceinline__ uint32_t *rows_of(const Params &P, const Ctx &c) {
     else return P.rows ? P.rows + (size_t)(c.cover - P.cover) * NW : nullptr;
 }
 
-template <typename W, int WT, bool GM, int NW>
-__device__ bool greedy_solve(const Params &P, Worker<W, WT, GM, NW> &w, Ctx &c) {
+template <class Wk>
+__device__ bool greedy_solve(const Params &P, Wk &w, Ctx &c) {
     w.cur_n = c.n;
     if (c.n == 0) {
         w.sync();
@@ -54,18 +67,19 @@ __device__ bool greedy_solve(const Params &P, Worker<W, WT, GM, NW> &w, Ctx &c) 
         w.sync();
         return false;
     }
-    w.stage(c, rows_of<NW>(P, c));
+    w.stage(c, rows_of<Wk::kRowWords>(P, c));
     w.load_root(c);
-    const int32_t m0 = w.hdr->m;
+    const int32_t m0 = w.node_m();
     for (;;) {
-        w.reduce(c, 0, kRuleDeg1 | kRuleDeg2Tri, false);
-        if (w.hdr->m == 0) break;
-        const int v = w.argmax(c);
+        reduce_fixpoint(w, c, 0, kRuleDeg1 | kRuleDeg2Tri, false);
+        if (w.node_m() == 0) break;
+        int dv;
+        const int v = w.argmax(c, dv);
         if (v < 0) break;  // unreachable: m > 0 implies a live vertex of degree >= 1
         w.take_vertex(c, v);
     }
     w.write_cover(c);
-    const int32_t S = w.hdr->S;
+    const int32_t S = w.node_S();
     w.sync();
     if (w.tid == 0) {
         __threadfence();
@@ -84,7 +98,8 @@ __device__ bool greedy_solve(const Params &P, Worker<W, WT, GM, NW> &w, Ctx &c) 
 template <typename W, int WT, bool GM, int NW>
 __global__ void __launch_bounds__(WT) greedy_kernel(Params P) {
     extern __shared__ __align__(16) uint8_t smem[];
-    Worker<W, WT, GM, NW> w(smem, P.n_max, P.csr_words, P.gstate + (size_t)blockIdx.x * (size_t)P.gstate_bytes);
+    typename WorkerSel<W, WT, GM, NW>::type w(smem, P.n_max, P.csr_words,
+                                              P.gstate + (size_t)blockIdx.x * (size_t)P.gstate_bytes);
     w.init_scratch(P.n_max);
     if (w.tid == 0) w.sc[kScB0] = ld_relaxed(&P.ctrl->status);
     w.sync();
@@ -194,9 +209,9 @@ __device__ __forceinline__ bool cover_lock(const Params &P, Problem *pr) {
 // An edgeless node passed the stop check: MVC lowers best (atomicMin) and, if it still holds the
 // smallest size under the cover lock, writes its cover; PVC raises the found flag and the first
 // worker to raise it writes the cover (Sec. IV-A).
-template <typename W, int WT, bool GM, int NW>
-__device__ void record_solution(const Params &P, Worker<W, WT, GM, NW> &w, const Ctx &c) {
-    const int32_t S = w.hdr->S;
+template <class Wk>
+__device__ void record_solution(const Params &P, Wk &w, const Ctx &c) {
+    const int32_t S = w.node_S();
     bool locked = false, write = false;
     if (w.tid == 0) {
         if (c.kind == kMVC) {
@@ -289,8 +304,8 @@ __device__ __forceinline__ int serve_wait(const Params &P, int &arg) {
 // 1 (a root is loaded), 2 (a worklist entry is loaded) or, in serving launches, 3 (a new request
 // is claimed; see serve_wait).  Sec. IV-C: the search is over when
 // the worklist is empty and no worker holds work, i.e. when no work unit is left.
-template <bool SERVE, typename W, int WT, bool GM, int NW>
-__device__ int acquire(const Params &P, Worker<W, WT, GM, NW> &w) {
+template <bool SERVE, class Wk>
+__device__ int acquire(const Params &P, Wk &w) {
     Control *ctrl = P.ctrl;
     if (w.tid == 0) {
         int result = 0, arg = 0;
@@ -385,7 +400,8 @@ constexpr int kMinBlocks(int wt) { return wt == 32 ? 16 : 1024 / wt; }
 template <typename W, int WT, bool GM, int NW, bool SERVE>
 __global__ void __launch_bounds__(kMaxThreads(WT), kMinBlocks(WT)) traverse_kernel(Params P) {
     extern __shared__ __align__(16) uint8_t smem[];
-    Worker<W, WT, GM, NW> w(smem, P.n_max, P.csr_words, P.gstate + (size_t)blockIdx.x * (size_t)P.gstate_bytes);
+    using Wk = typename WorkerSel<W, WT, GM, NW>::type;
+    Wk w(smem, P.n_max, P.csr_words, P.gstate + (size_t)blockIdx.x * (size_t)P.gstate_bytes);
     w.init_scratch(P.n_max);
     Control *ctrl = P.ctrl;
     w.dbg = ctrl;
@@ -396,6 +412,9 @@ __global__ void __launch_bounds__(kMaxThreads(WT), kMinBlocks(WT)) traverse_kern
     int cur = -1;
     bool stop = false;
     bool fresh = true;  // the next node needs a fresh snapshot (its problem may be new)
+    uint32_t nn = 0;    // bit-row workers: nodes expanded (its low bits pace the periodic work)
+    int32_t bound = 0;  // snapshot: best (MVC) or k (PVC), one value for a whole node (reading R3)
+    int32_t fill = 0;   // snapshot: worklist entries waiting
     Ctx c;
     c.n = 0;
 
@@ -412,10 +431,8 @@ __global__ void __launch_bounds__(kMaxThreads(WT), kMinBlocks(WT)) traverse_kern
             const long long t_pop = VC_CYC();
             --top;
             w.load_entry(stack + (size_t)top * eb, eb, P.n_max);
-            if constexpr (NW > 0) w.init_live(c);
-            if (w.tid == 0) {
-                w.tally[kTPops] += 1;
-            }
+            w.node_loaded(c);
+            if (w.tid == 0) w.tally[kTPops] += 1;
             VC_CYC_ADD(w, kPPop, t_pop);
         } else {
             if (cur >= 0 && w.tid == 0) release_unit(P, cur);
@@ -436,20 +453,21 @@ __global__ void __launch_bounds__(kMaxThreads(WT), kMinBlocks(WT)) traverse_kern
                     w.load_root(c);
                 }
             } else {
-                cur = w.hdr->problem;
+                cur = w.node_problem();
                 VC_CHECK(ctrl, cur >= 0 && cur < P.num_problems, 1, cur, { stop = true; break; });
                 c = make_ctx(P, cur);
                 VC_CHECK(ctrl, c.n >= 0 && c.n <= P.n_max, 14, c.n, { stop = true; break; });
                 w.cur_n = c.n;
-                w.template stage<false>(c, rows_of<NW>(P, c));
-                if constexpr (NW > 0) w.init_live(c);
+                w.template stage<false>(c, rows_of<Wk::kRowWords>(P, c));
+                w.node_loaded(c);
             }
         }
-        VC_CHECK(ctrl, w.hdr->branch < c.n, 13, w.hdr->branch, { stop = true; break; });
-        if (w.hdr->branch >= 0) {  // a lazily stored N(v) child: apply the removal now
+        const int32_t br = w.node_branch();
+        VC_CHECK(ctrl, br < c.n, 13, br, { stop = true; break; });
+        if (br >= 0) {  // a lazily stored N(v) child: apply the removal now
             const long long t_tn = VC_CYC();
-            w.take_neighbourhood(c, w.hdr->branch);
-            if (w.tid == 0) w.hdr->branch = -1;
+            w.take_neighbourhood(c, br);
+            w.clear_branch();
             VC_CYC_ADD(w, kPTakeN, t_tn);
         }
 
@@ -459,41 +477,74 @@ __global__ void __launch_bounds__(kMaxThreads(WT), kMinBlocks(WT)) traverse_kern
             // The snapshot of best / found / status / worklist fill is re-read for every 16th node
             // and for the first node after acquiring work (reading R3: a stale, larger best only
             // weakens pruning).  Re-reading it for every node cost 2.5 % of the batch time, and for
-            // every fourth node 0.5 %.
-            if (w.tid == 0) {
-                const unsigned long long nn = ++w.tally[kTNodes];
-                if ((nn & 31) == 0) atomicAdd(&ctrl->heartbeat, 1u);
-                // A busy worker also honours the caller's cancel flag (every 1024 nodes: the flag
-                // may live in host memory); the status read just below then stops it.
-                if ((nn & 1023) == 0 && P.cancel && *P.cancel) raise_status(ctrl, VC_ECANCELLED);
-                if (fresh || (nn & (kSnapshotEvery - 1)) == 0) {
-                    w.sc[kScB0] = (c.kind == kMVC) ? ld_relaxed(&c.prob->best) : c.k;
-                    w.sc[kScB1] = (c.kind == kPVC) ? ld_relaxed(&c.prob->found) : 0;
-                    w.sc[kScB2] = ld_relaxed(&ctrl->status);
-                    w.sc[kScWlHint] = ld_relaxed(&ctrl->wl_count);
+            // every fourth node 0.5 %.  Busy workers bump the heartbeat every 32 nodes and honour
+            // the caller's cancel flag every 1024 (the flag may live in host memory; the status
+            // read of the next snapshot then stops the worker).
+            if constexpr (Wk::kRowWords > 0) {
+                // One warp, node in registers: the node count and the snapshot live in registers,
+                // every lane reads the shared words itself, and the found flag and the status are
+                // looked at only when they are re-read.
+                ++nn;
+                if ((nn & 31u) == 0u && w.tid == 0) atomicAdd(&ctrl->heartbeat, 1u);
+                if ((nn & 1023u) == 0u) {
+                    w.flush_counts();  // statistics kept in registers go to the shared tallies
+                    if (w.tid == 0) {
+                        w.tally[kTNodes] += 1024ull;
+                        if (P.cancel && *P.cancel) raise_status(ctrl, VC_ECANCELLED);
+                    }
+                }
+                if (fresh || (nn & (kSnapshotEvery - 1u)) == 0u) {
+                    bound = (c.kind == kMVC) ? ld_relaxed(&c.prob->best) : c.k;
+                    const int32_t found = (c.kind == kPVC) ? ld_relaxed(&c.prob->found) : 0;
+                    const int32_t status = ld_relaxed(&ctrl->status);
+                    fill = ld_relaxed(&ctrl->wl_count);
+                    fresh = false;
+                    if (status != VC_OK) {
+                        stop = true;
+                        break;
+                    }
+                    if (found) {  // PVC already answered: drop this problem's remaining work
+                        w.discard_pending();
+                        top = 0;
+                        break;
+                    }
+                }
+            } else {
+                // Node in shared memory: thread 0 keeps the count and the snapshot in shared
+                // memory (registers are scarcer here), and the worker reads them after a barrier.
+                if (w.tid == 0) {
+                    const unsigned long long n64 = ++w.tally[kTNodes];
+                    if ((n64 & 31) == 0) atomicAdd(&ctrl->heartbeat, 1u);
+                    if ((n64 & 1023) == 0 && P.cancel && *P.cancel) raise_status(ctrl, VC_ECANCELLED);
+                    if (fresh || (n64 & (kSnapshotEvery - 1)) == 0) {
+                        w.sc[kScB0] = (c.kind == kMVC) ? ld_relaxed(&c.prob->best) : c.k;
+                        w.sc[kScB1] = (c.kind == kPVC) ? ld_relaxed(&c.prob->found) : 0;
+                        w.sc[kScB2] = ld_relaxed(&ctrl->status);
+                        w.sc[kScWlHint] = ld_relaxed(&ctrl->wl_count);
+                    }
+                }
+                fresh = false;
+                w.sync();
+                bound = w.sc[kScB0];
+                if (w.sc[kScB2] != VC_OK) {
+                    stop = true;
+                    break;
+                }
+                if (w.sc[kScB1]) {  // PVC already answered: drop this problem's remaining work
+                    w.discard_pending();
+                    top = 0;
+                    break;
                 }
             }
-            fresh = false;
-            w.sync();
-            const int32_t bound = w.sc[kScB0];  // one bound for the whole node (reading R3)
             VC_CYC_ADD(w, kPHeader, t_hdr);
-            if (w.sc[kScB2] != VC_OK) {
-                stop = true;
-                break;
-            }
-            if (w.sc[kScB1]) {  // PVC already answered: drop this problem's remaining work
-                w.discard_pending();
-                top = 0;
-                break;
-            }
             const unsigned long long t_red = VC_TRACE_NOW();
-            const bool reduced_out = w.reduce(c, bound, kRuleAll, true);
+            const bool reduced_out = reduce_fixpoint(w, c, bound, kRuleAll, true);
             const long long t_stop = VC_CYC();
             const bool pruned = reduced_out || w.must_stop(c, bound);
             VC_CYC_ADD(w, kPStop, t_stop);
             VC_TRACE_ADD(w, kTReduceNs, t_red);
             if (pruned) break;
-            if (w.hdr->m == 0) {
+            if (w.node_m() == 0) {
                 const unsigned long long t_sol = VC_TRACE_NOW();
                 const long long t_solc = VC_CYC();
                 record_solution(P, w, c);
@@ -503,7 +554,8 @@ __global__ void __launch_bounds__(kMaxThreads(WT), kMinBlocks(WT)) traverse_kern
             }
             const unsigned long long t_br = VC_TRACE_NOW();
             const long long t_am = VC_CYC();
-            const int v = w.argmax(c);
+            int dv;
+            const int v = w.argmax(c, dv);
             VC_CYC_ADD(w, kPArgmax, t_am);
             const long long t_store = VC_CYC();
             if (v < 0) {  // unreachable: m > 0 implies a live vertex of degree >= 1
@@ -511,26 +563,35 @@ __global__ void __launch_bounds__(kMaxThreads(WT), kMinBlocks(WT)) traverse_kern
                 stop = true;
                 break;
             }
-            const int dv = w.deg(v);
-            const int32_t S = w.hdr->S;
+            const int32_t S = w.node_S();
             // The N(v) child puts dv vertices into S; skip it when that alone prunes it.
             const bool keep = (c.kind == kMVC) ? (S + dv < bound) : (S + dv <= c.k);
             if (keep) {
-                if (w.tid == 0) {
-                    const long long pos = wl_reserve(P, w.sc[kScWlHint]);
-                    w.sc[kScB3] = pos >= 0;
-                    w.sc[kScB4] = (int32_t)(uint32_t)(pos >= 0 ? pos : 0);
+                int32_t donate, pos;
+                if constexpr (Wk::kRowWords > 0) {
+                    long long t = -1;
+                    if (w.tid == 0) t = wl_reserve(P, fill);
+                    donate = __shfl_sync(kFull, t >= 0 ? 1 : 0, 0);
+                    pos = __shfl_sync(kFull, (int32_t)(uint32_t)(t >= 0 ? t : 0), 0);
+                } else {
+                    if (w.tid == 0) {
+                        const long long t = wl_reserve(P, w.sc[kScWlHint]);
+                        w.sc[kScB3] = t >= 0;
+                        w.sc[kScB4] = (int32_t)(uint32_t)(t >= 0 ? t : 0);
+                    }
+                    w.sync();
+                    donate = w.sc[kScB3];
+                    pos = w.sc[kScB4];
                 }
-                w.sync();
-                if (w.sc[kScB3]) {  // donate (Sec. IV-A: the worklist is below its threshold)
-                    const uint32_t pos = (uint32_t)w.sc[kScB4];
-                    w.store_entry(P.wl_slots + (size_t)(pos & wl_mask) * eb, eb, v);
+                if (donate) {  // donate (Sec. IV-A: the worklist is below its threshold)
+                    const uint32_t ticket = (uint32_t)pos;
+                    w.store_entry(P.wl_slots + (size_t)(ticket & wl_mask) * eb, eb, v);
                     w.sync();  // every thread's part of the entry is written ...
                     if (w.tid == 0) {
                         __threadfence();  // ... and ordered before the publication below
                         atomicAdd(&c.prob->units, 1);
                         atomicAdd(&ctrl->units_total, 1);
-                        st_release_u32(&P.wl_seq[pos & wl_mask], pos + 1u);
+                        st_release_u32(&P.wl_seq[ticket & wl_mask], ticket + 1u);
                         atomicAdd(&ctrl->wl_count, 1);
                         w.tally[kTDonations] += 1;
                     }
@@ -558,8 +619,10 @@ __global__ void __launch_bounds__(kMaxThreads(WT), kMinBlocks(WT)) traverse_kern
     }
 
     // ---- statistics ----
+    w.flush_counts();
     w.sync();
     if (w.tid == 0) {
+        if constexpr (Wk::kRowWords > 0) w.tally[kTNodes] += (unsigned long long)(nn & 1023u);
         const unsigned long long *T = w.tally;
         atomicAdd(&ctrl->nodes, T[kTNodes]);
         atomicAdd(&ctrl->stack_pushes, T[kTPushes]);
@@ -582,13 +645,13 @@ __global__ void __launch_bounds__(kMaxThreads(WT), kMinBlocks(WT)) traverse_kern
 }
 
 // ------------------------------------------------------------------------------------------------
-// One node's reduction (tests): reads an int32 degree array, reduces it to the fixpoint in shared
-// memory (no early exit, like the oracle), writes it back with |S|, m and the stop verdict.
+// One node's reduction (tests): reads an int32 degree array, reduces it to the fixpoint (no early
+// exit, like the oracle), writes it back with |S|, m and the stop verdict.
 // ------------------------------------------------------------------------------------------------
 template <typename W, int WT, bool GM, int NW>
 __global__ void __launch_bounds__(WT) reduce_node_kernel(ReduceParams R) {
     extern __shared__ __align__(16) uint8_t smem[];
-    Worker<W, WT, GM, NW> w(smem, R.n, 0, R.gstate);
+    typename WorkerSel<W, WT, GM, NW>::type w(smem, R.n, 0, R.gstate);
     w.init_scratch(R.n);
     Ctx c;
     c.off = R.offsets;
@@ -599,26 +662,19 @@ __global__ void __launch_bounds__(WT) reduce_node_kernel(ReduceParams R) {
     c.kind = R.problem;
     c.k = R.bound;
     c.index = 0;
-    if constexpr (NW > 0) w.stage(c, nullptr);  // bit rows built from the CSR
-    for (int v = w.tid; v < R.n; v += WT) w.d[v] = (W)R.deg[v];  // plain stores; read after sync()
-    if (R.branch == -1) w.dirty_all(R.n);  // a state from outside: every vertex is looked at
-    if (w.tid == 0) {
-        w.hdr->problem = 0;
-        w.hdr->S = R.io[0];
-        w.hdr->m = R.io[1];
-        w.hdr->branch = -1;
-    }
-    w.sync();
-    if constexpr (NW > 0) w.init_live(c);
-    // A branch from a fixpoint state starts clean, like a stored node in the traversal.
+    w.cur_n = R.n;
+    w.stage(c, nullptr);  // bit rows built from the CSR (CSR-walk workers stage nothing here)
+    // A state from outside has every vertex looked at; a branch from a fixpoint state starts
+    // clean, like a stored node in the traversal.
+    w.load_plain(c, R.deg, R.io[0], R.io[1], R.branch == -1);
     if (R.branch >= 0) w.take_vertex(c, R.branch);
     else if (R.branch <= -2) w.take_neighbourhood(c, -2 - R.branch);
-    w.reduce(c, R.bound, R.rules, false);
+    reduce_fixpoint(w, c, R.bound, R.rules, false);
     const bool pruned = w.must_stop(c, R.bound);
-    for (int v = w.tid; v < R.n; v += WT) R.deg[v] = w.deg(v);
+    w.save_plain(c, R.deg);
     if (w.tid == 0) {
-        R.io[0] = w.hdr->S;
-        R.io[1] = w.hdr->m;
+        R.io[0] = w.node_S();
+        R.io[1] = w.node_m();
         R.io[2] = pruned ? 1 : 0;
     }
 }
