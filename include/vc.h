@@ -185,8 +185,14 @@ int vc_reduce_node(const vc_graph *g, int32_t *deg, int32_t *S, int32_t *m, int3
  *   - g must be on the device (on_device = 1) with n <= VC_NOALLOC_MAX_N; larger graphs and host
  *     pointers are rejected with VC_EINVAL.  cover_out (n int32, device, may be NULL) and
  *     *cover_size_out (host) receive the result; cfg and stats may be NULL.
- *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
- *     that device current; make that first call before capturing any stream.
+ *   - The first call on a device does a one-time set-up: it looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current.  Make that first call before any stream
+ *     capture begins on the device.
+ *   - cfg fields it reads: worker_threads, num_workers, donate_threshold, idle_timeout_ns,
+ *     skip_validation, cancel, and stage_csr 0 or -1.  Entries are always 16-bit, the node stays
+ *     in shared memory, the workers walk the CSR and the worklist is a fixed ring of 1024 entries:
+ *     width 32, node_in_global 1, bit_rows 1, stage_csr 1 or any other worklist_capacity return
+ *     VC_EINVAL.
  *   - All calls of a process share the one array, and each call resets what must start from a
  *     known value.  Calls are serialised: each holds a process-wide lock until its GPU work has
  *     finished, error returns included, so calls from any host threads and streams of one process

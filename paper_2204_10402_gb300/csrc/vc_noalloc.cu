@@ -86,7 +86,12 @@ extern "C" int vc_mvc_noalloc(const vc_graph *g, const vc_config *cfg_in, void *
     vc_config cfg;
     std::memset(&cfg, 0, sizeof(cfg));
     if (cfg_in) cfg = *cfg_in;
-    if (cfg.node_in_global > 0) return VC_EINVAL;  // the node stays in shared memory here
+    // Settings this entry point cannot honour are errors, not silently replaced: the node stays in
+    // shared memory, entries are 16-bit, the workers walk the CSR with at most its offsets staged,
+    // and the worklist is the array's fixed ring.
+    if (cfg.node_in_global > 0 || (cfg.width != 0 && cfg.width != 16) || cfg.bit_rows > 0 || cfg.stage_csr > 0 ||
+        (cfg.worklist_capacity != 0 && cfg.worklist_capacity != kNoAllocWorklist))
+        return VC_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
 
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
@@ -159,7 +164,9 @@ extern "C" int vc_mvc_noalloc(const vc_graph *g, const vc_config *cfg_in, void *
     P.ctrl = d_ctrl;
     P.cover = d_cover;
     P.wl_capacity = kNoAllocWorklist;
-    P.wl_threshold = kNoAllocWorklist / 2;
+    // Donation threshold as in vc_mvc: a fraction of the ring (0: one half), negative = never donate.
+    const float frac = cfg.donate_threshold > 0.f ? std::min(cfg.donate_threshold, 1.f) : 0.5f;
+    P.wl_threshold = cfg.donate_threshold < 0.f ? 0 : std::max(1, (int)(frac * (float)kNoAllocWorklist));
     P.csr_words = csr_words;
     P.idle_timeout_ns = cfg.idle_timeout_ns > 0 ? cfg.idle_timeout_ns : 20000000000ll;
     P.cancel = cfg.cancel;
@@ -224,6 +231,8 @@ extern "C" int vc_mvc_noalloc(const vc_graph *g, const vc_config *cfg_in, void *
         stats->workers = (int32_t)workers;
         stats->worker_threads = wt;
         stats->width = 16;
+        stats->csr_staged = csr_words > 0 ? 1 : 0;
+        stats->stack_depth = (int32_t)depth;
         stats->status = h_ctrl.status;
     }
     return VC_OK;

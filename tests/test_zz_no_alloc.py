@@ -46,6 +46,22 @@ def test_noalloc_matches_allocating_entry_point(vc):
             cover = a.cover.cpu().numpy().astype(bool)
             assert cover.sum() == a.value
             assert oracle.verify_cover(g, cover)
+            assert a.stats["stack_depth"] > 0 and a.stats["width"] == 16
+
+
+def test_noalloc_rejects_settings_it_cannot_honour(vc):
+    import torch
+    g = G.gnp(60, 0.10, 0)
+    off, nbr = torch.from_numpy(g.offsets).cuda(), torch.from_numpy(g.neighbors).cuda()
+    want = vc.mvc(off, nbr).value
+    for bad in (dict(width=32), dict(bit_rows=1), dict(stage_csr=1), dict(node_in_global=1),
+                dict(worklist_capacity=4096)):
+        with pytest.raises(vc.VCError) as e:
+            vc.mvc_noalloc(off, nbr, config=vc.make_config(**bad))
+        assert e.value.code == vc.VC_EINVAL, bad
+    for ok in (dict(width=16), dict(stage_csr=-1), dict(worklist_capacity=1024), dict(donate_threshold=-1.0),
+               dict(donate_threshold=1.0)):
+        assert vc.mvc_noalloc(off, nbr, config=vc.make_config(**ok)).value == want, ok
 
 
 def test_noalloc_rejects_oversize_and_host_inputs(vc):
