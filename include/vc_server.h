@@ -51,6 +51,8 @@ typedef struct {
     int64_t nodes_visited;                  /* tree nodes over all finished launches */
     int32_t workers, worker_threads, slots_per_epoch;
     int64_t arena_bytes;
+    int64_t records;                        /* requests whose records the server still holds (not yet
+                                               released with vc_server_release) */
 } vc_server_counters;
 
 /* Creates a server on the current device.  device_bytes_budget (0 = 8 GiB) bounds the device
@@ -68,6 +70,12 @@ int vc_server_submit(vc_server *server, const vc_graph *g, int32_t kind, int32_t
 
 /* Reads a request's state (see vc_request_info). */
 int vc_server_poll(vc_server *server, uint64_t request_id, vc_request_info *info);
+
+/* Forgets a finished request: its record is freed and its id becomes unknown (a later poll or
+ * release of it returns VC_EINVAL).  A request that has not finished cannot be released
+ * (VC_EINVAL).  A long-running server should release every request once its answer has been read;
+ * records that are never released are freed by vc_server_destroy. */
+int vc_server_release(vc_server *server, uint64_t request_id);
 
 /* Waits until every submitted request has finished (timeout_ms <= 0: no limit; VC_ETIMEOUT if the
  * limit passes first). */

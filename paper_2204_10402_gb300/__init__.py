@@ -28,8 +28,8 @@ RULE_DEG1, RULE_DEG2TRI, RULE_HIGH, RULE_ALL = 1, 2, 4, 7
 
 EXPORTED = ["vc_mvc", "vc_pvc", "vc_mvc_batch", "vc_greedy", "vc_reduce_node", "vc_last_sm_nodes",
             "vc_release", "vc_strerror", "vc_version", "vc_mvc_noalloc",
-            "vc_server_create", "vc_server_submit", "vc_server_poll", "vc_server_drain", "vc_server_stats",
-            "vc_server_destroy", "vc_plan_create_mvc_batch", "vc_plan_launch", "vc_plan_results",
+            "vc_server_create", "vc_server_submit", "vc_server_poll", "vc_server_release", "vc_server_drain",
+            "vc_server_stats", "vc_server_destroy", "vc_plan_create_mvc_batch", "vc_plan_launch", "vc_plan_results",
             "vc_plan_destroy", "vc_l2_copy_probe"]
 NOALLOC_MAX_N = 512
 
@@ -86,7 +86,7 @@ class ServerCounters(ctypes.Structure):
     _fields_ = [("completed", ctypes.c_int64), ("pending", ctypes.c_int64), ("in_flight", ctypes.c_int64),
                 ("launches", ctypes.c_int64), ("epochs", ctypes.c_int64), ("nodes_visited", ctypes.c_int64),
                 ("workers", ctypes.c_int32), ("worker_threads", ctypes.c_int32),
-                ("slots_per_epoch", ctypes.c_int32), ("arena_bytes", ctypes.c_int64)]
+                ("slots_per_epoch", ctypes.c_int32), ("arena_bytes", ctypes.c_int64), ("records", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -127,6 +127,7 @@ def load(path: str | None = None):
     lib.vc_server_create.argtypes = [cp, ctypes.c_size_t, i32, ctypes.POINTER(ctypes.c_void_p)]
     lib.vc_server_submit.argtypes = [P, gp, i32, i32, ctypes.POINTER(ctypes.c_uint64)]
     lib.vc_server_poll.argtypes = [P, ctypes.c_uint64, ctypes.POINTER(RequestInfo)]
+    lib.vc_server_release.argtypes = [P, ctypes.c_uint64]
     lib.vc_server_drain.argtypes = [P, i64]
     lib.vc_server_stats.argtypes = [P, ctypes.POINTER(ServerCounters)]
     lib.vc_server_destroy.argtypes = [P]
@@ -141,7 +142,7 @@ def load(path: str | None = None):
     lib.vc_version.argtypes = []
     for name in ("vc_mvc", "vc_pvc", "vc_mvc_batch", "vc_greedy", "vc_reduce_node", "vc_last_sm_nodes",
                  "vc_release", "vc_version", "vc_mvc_noalloc", "vc_server_create", "vc_server_submit",
-                 "vc_server_poll", "vc_server_drain", "vc_server_stats", "vc_server_destroy",
+                 "vc_server_poll", "vc_server_release", "vc_server_drain", "vc_server_stats", "vc_server_destroy",
                  "vc_plan_create_mvc_batch", "vc_plan_launch", "vc_plan_results", "vc_plan_destroy"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
@@ -423,10 +424,16 @@ class Server:
                "vc_server_submit")
         return int(rid.value)
 
-    def poll(self, rid: int) -> dict:
+    def poll(self, rid: int, release: bool = False) -> dict:
+        """The request's state; with release=True a finished request is also forgotten."""
         info = RequestInfo()
         _check(self._lib.vc_server_poll(self._h, ctypes.c_uint64(rid), ctypes.byref(info)), "vc_server_poll")
+        if release and info.done:
+            self.release(rid)
         return info.as_dict()
+
+    def release(self, rid: int):
+        _check(self._lib.vc_server_release(self._h, ctypes.c_uint64(rid)), "vc_server_release")
 
     def drain(self, timeout_ms: int = 0):
         _check(self._lib.vc_server_drain(self._h, int(timeout_ms)), "vc_server_drain")

@@ -565,6 +565,16 @@ int vc_server_poll(vc_server *s, uint64_t request_id, vc_request_info *info) {
     return VC_OK;
 }
 
+int vc_server_release(vc_server *s, uint64_t request_id) {
+    if (!s) return VC_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->all.find(request_id);
+    if (it == s->all.end() || it->second->state != 2) return VC_EINVAL;  // unknown, or not finished
+    delete it->second;  // a finished request is in no queue: nothing else refers to it
+    s->all.erase(it);
+    return VC_OK;
+}
+
 int vc_server_drain(vc_server *s, int64_t timeout_ms) {
     if (!s) return VC_EINVAL;
     std::unique_lock<std::mutex> lk(s->mu);
@@ -592,6 +602,7 @@ int vc_server_stats(vc_server *s, vc_server_counters *out) {
     out->worker_threads = s->wt;
     out->slots_per_epoch = s->slots;
     out->arena_bytes = (int64_t)s->arena_bytes;
+    out->records = (int64_t)s->all.size();
     return VC_OK;
 }
 

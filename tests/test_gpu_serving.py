@@ -135,3 +135,29 @@ def test_degenerate_requests(vc):
         infos = [srv.poll(i) for i in ids] + [srv.poll(rid.value)]
     assert all(x["done"] and x["status"] == 0 for x in infos)
     assert [x["answer"] for x in infos] == [c[3] for c in cases] + [0]
+
+
+def test_released_requests_leave_no_records(vc):
+    # A long-running server keeps a record per request until the caller releases it: polling with
+    # release keeps the held records bounded, and a released id is unknown afterwards.
+    reqs = mixed_requests(40, 150000)
+    with vc.Server(max_n=1000) as srv:
+        held = []
+        for rnd in range(5):
+            ids = [srv.submit(g.offsets, g.neighbors, kind, k) for g, kind, k, _ in reqs]
+            srv.drain(timeout_ms=120000)
+            for rid, (_, _, _, want) in zip(ids, reqs):
+                info = srv.poll(rid, release=True)
+                assert info["done"] == 1 and info["status"] == 0 and info["answer"] == want
+            held.append(srv.stats()["records"])
+        assert held == [0] * 5
+        with pytest.raises(vc.VCError) as e:
+            srv.poll(ids[0])
+        assert e.value.code == vc.VC_EINVAL
+        with pytest.raises(vc.VCError):
+            srv.release(ids[0])
+        rid = srv.submit(reqs[0][0].offsets, reqs[0][0].neighbors, reqs[0][1], reqs[0][2])
+        srv.drain(timeout_ms=120000)
+        assert srv.stats()["records"] == 1
+        srv.release(rid)
+        assert srv.stats()["records"] == 0
