@@ -1,5 +1,6 @@
 """Autotuner search logic (CPU, fake measurements) and one GPU tuning run on a small batch."""
 import math
+import os
 
 import pytest
 
@@ -61,3 +62,7 @@ def test_tune_small_batch(tmp_path, monkeypatch):
     sizes, _, _ = vc.mvc_batch(b.vtx, b.edge, off, nbr, config=got, want_covers=False)
     ref, _, _ = vc.mvc_batch(b.vtx, b.edge, off, nbr, want_covers=False)
     assert list(sizes) == list(ref)
+    # Both against the oracle's stored answers for the same 256 graphs (tests/golden, oracle only).
+    gold = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "batch4096_mvc.txt")
+    want = [int(l.split()[3]) for l in open(gold) if not l.startswith("#")][:256]
+    assert list(sizes) == want
