@@ -1,19 +1,26 @@
 /*
  * vc_server.h - serving exact vertex cover with continuous batching (libvc).
  *
- * A server keeps one persistent traversal launch (the hybrid stack + worklist search of Sec. IV-A,
- * rules of Sec. II-B / IV-D, termination of Sec. IV-C) running while requests arrive.  Requests
- * admitted while others are being searched join the running launch: idle workers claim them, run
- * their greedy bound (Sec. II-B) and search them through the shared worklist, whose entries carry
- * the request's slot, so the work of many requests overlaps on the device.  The paper solves one
- * graph per launch; the serving layer is this library's own.
+ * A server keeps a persistent traversal launch (the hybrid stack + worklist search of Sec. IV-A,
+ * rules of Sec. II-B / IV-D, termination of Sec. IV-C) running per size class while requests
+ * arrive.  Requests admitted while others are being searched join the running launch of their
+ * class: idle workers claim them, run their greedy bound (Sec. II-B) and search them through the
+ * class's worklist, whose entries carry the request's slot, so the work of many requests overlaps
+ * on the device.  The paper solves one graph per launch; the serving layer is this library's own.
  *
- * Admission: every request reserves a slot and a range of the device graph arena (its CSR and
- * cover mask).  Stacks and worklist are sized once, at creation, for graphs of up to max_n
- * vertices (depth max_n + 3 entries of the degree-array size per worker), so any accepted request
- * fits them.  A request whose bytes do not fit the arena right now waits in a host queue and is
- * admitted when earlier requests finish; it is never refused for lack of room unless it alone is
- * larger than the whole arena.
+ * Size classes: graphs of at most 128 vertices run on one-warp bit-row workers (the node in
+ * registers, the adjacency as bit rows in shared memory), larger ones on CSR-walk workers sized for
+ * max_n.  The two classes' launches run side by side, each on half of every SM's thread slots and
+ * with its own stacks, worklist and arena.  cfg->bit_rows = -1 serves every request on CSR walks
+ * (one class); cfg->worker_threads, width, worklist_capacity and donate_threshold apply to the
+ * CSR-walk class.
+ *
+ * Admission: every request reserves a slot and a range of its class's device graph arena (its
+ * CSR and cover mask).  Stacks and worklist are reserved per class at creation for the class's
+ * largest graph (depth n + 3 entries of the degree-array size per worker, n = 128 or max_n), so
+ * any accepted request fits them.  A request whose bytes do not fit the arena right now waits in a
+ * host queue and is admitted when earlier requests of its class finish; it is never refused for
+ * lack of room unless it alone is larger than the whole arena.
  *
  * Graphs are copied at submission (host pointers only; same CSR rules as vc.h, checked on the host);
  * the caller's buffers can be reused as soon as vc_server_submit returns.  All functions are safe
@@ -53,12 +60,19 @@ typedef struct {
     int64_t arena_bytes;
     int64_t records;                        /* requests whose records the server still holds (not yet
                                                released with vc_server_release) */
+    int32_t classes;                        /* size classes, each its own persistent launch (1 or 2) */
+    int32_t small_max_n;                    /* largest graph of the bit-row class (0: no such class) */
+    int32_t small_workers;                  /* one-warp workers of the bit-row class (also in workers) */
+    int32_t reserved;
 } vc_server_counters;
 
 /* Creates a server on the current device.  device_bytes_budget (0 = 8 GiB) bounds the device
- * memory it holds: half goes to the per-worker stacks (which sets the worker count), a quarter to
- * the graph arena.  max_n is the largest graph it accepts.  cfg (may be NULL) picks the worker size,
- * width, worklist capacity and donation threshold as in vc.h. */
+ * memory it holds: an eighth goes to the bit-row class when there are two, the rest to the other;
+ * within a class, half goes to the per-worker stacks (which sets the worker count, up to the SM
+ * slots the class has), a quarter to the graph arena (and, in the bit-row class, the bit rows).
+ * max_n is the largest graph it accepts.  cfg (may be NULL) picks the CSR-walk class's worker size,
+ * width, worklist capacity and donation threshold as in vc.h; bit_rows = 1 and node_in_global = 1
+ * are VC_EINVAL. */
 int vc_server_create(const vc_config *cfg, size_t device_bytes_budget, int32_t max_n, vc_server **server);
 
 /* Queues a request: kind 0 = MVC, 1 = PVC with parameter k.  Returns at once with its id.  The

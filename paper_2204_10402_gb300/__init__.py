@@ -86,7 +86,9 @@ class ServerCounters(ctypes.Structure):
     _fields_ = [("completed", ctypes.c_int64), ("pending", ctypes.c_int64), ("in_flight", ctypes.c_int64),
                 ("launches", ctypes.c_int64), ("epochs", ctypes.c_int64), ("nodes_visited", ctypes.c_int64),
                 ("workers", ctypes.c_int32), ("worker_threads", ctypes.c_int32),
-                ("slots_per_epoch", ctypes.c_int32), ("arena_bytes", ctypes.c_int64), ("records", ctypes.c_int64)]
+                ("slots_per_epoch", ctypes.c_int32), ("arena_bytes", ctypes.c_int64), ("records", ctypes.c_int64),
+                ("classes", ctypes.c_int32), ("small_max_n", ctypes.c_int32), ("small_workers", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}

@@ -46,8 +46,8 @@ struct LaunchImpl {
         return launch_status();
     }
     static int traverse(int wt, int grid, int smem, cudaStream_t s, const Params &P) {
-        if (P.serving) {  // the server's launch: shared-memory nodes, CSR walks
-            if constexpr (GM || NW > 0) {
+        if (P.serving) {  // the server's launches: CSR walks, or 4-word bit rows (graphs of <= 128 vertices)
+            if constexpr (GM || (NW != 0 && NW != 4)) {
                 return VC_EINVAL;
             } else {
                 VC_WT_SWITCH(wt, {

@@ -64,7 +64,24 @@ def test_mix_equals_alone_and_oracle(vc):
         st = srv.stats()
     assert all(x["done"] and x["status"] == 0 for x in infos)
     assert [x["answer"] for x in infos] == alone
-    assert st["completed"] == len(reqs) and st["launches"] >= 1
+    assert st["completed"] == len(reqs) and st["launches"] >= 2
+    # Two size classes: graphs of at most 128 vertices on bit-row workers, the rest on CSR walks.
+    assert st["classes"] == 2 and st["small_max_n"] == 128 and 0 < st["small_workers"] < st["workers"]
+    assert any(g.n <= 128 for g, *_ in reqs) and any(g.n > 128 for g, *_ in reqs)
+
+
+def test_one_class_with_csr_walks_only(vc):
+    # bit_rows = -1 serves every request on CSR-walk workers: one class, the same answers.
+    reqs = mixed_requests(40, 125000)
+    with vc.Server(max_n=1000, config=vc.make_config(bit_rows=-1)) as srv:
+        ids = [srv.submit(g.offsets, g.neighbors, kind, k) for g, kind, k, _ in reqs]
+        srv.drain(timeout_ms=120000)
+        infos = [srv.poll(i) for i in ids]
+        st = srv.stats()
+    assert [x["answer"] for x in infos] == [r[3] for r in reqs]
+    assert st["classes"] == 1 and st["small_max_n"] == 0 and st["small_workers"] == 0
+    with pytest.raises(vc.VCError):
+        vc.Server(max_n=100, config=vc.make_config(bit_rows=1))
 
 
 def test_trickled_requests_join_a_running_launch(vc):
