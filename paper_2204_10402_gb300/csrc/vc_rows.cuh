@@ -259,10 +259,12 @@ struct RowWorker {
         for (int k = 0; k < NW; ++k) pend[k] = 0u;
     }
 
-    // Moves the chosen set into S.  Few chosen vertices (the "v" child, most rule removals): each
-    // one's live neighbours outside the set lose one degree.  More: every live vertex outside the
-    // set recounts its degree as popc(row & live').  Either way m = (sum of live degrees) / 2 and
-    // the degree bound is recomputed; every vertex whose degree changed becomes dirty.
+    // Moves the chosen set into S.  One chosen vertex u (the "v" child, most single rule
+    // removals): u's live neighbours lose one degree each and m loses deg(u); the degree bound
+    // still holds.  Two or three: each one's live neighbours outside the set lose one degree.
+    // More: every live vertex outside the set recounts its degree as popc(row & live').  With
+    // several, m = (sum of live degrees) / 2 and the degree bound is recomputed.  Every vertex
+    // whose degree changed becomes dirty.
     __device__ void apply(const Ctx &c) {
         const long long t1 = VC_CYC();
         uint32_t nl[NW];
@@ -271,6 +273,30 @@ struct RowWorker {
         for (int k = 0; k < NW; ++k) {
             nl[k] = live[k] & ~pend[k];
             cnt += __popc(pend[k]);
+        }
+        if (cnt == 1) {
+            int u = 0;
+#pragma unroll
+            for (int w = NW - 1; w >= 0; --w)
+                if (pend[w]) u = 32 * w + __ffs(pend[w]) - 1;
+            uint32_t r[NW];
+            row(u, r);
+            int du = 0;
+#pragma unroll
+            for (int k = 0; k < NW; ++k) {
+                const uint32_t hit = r[k] & nl[k];
+                const bool mine = (pend[k] >> lane) & 1u;
+                dg[k] = mine ? -1 : dg[k] - (int)((hit >> lane) & 1u);
+                dirty2[k] |= hit;
+                du += __popc(hit);
+                live[k] = nl[k];
+                pend[k] = 0u;
+            }
+            if (lane == 0) words += deg0[u];
+            m -= du;
+            S += 1;
+            VC_CYC_ADD(*this, kPApply, t1);
+            return;
         }
         if (cnt <= 3) {
             uint32_t t[NW];
@@ -359,10 +385,13 @@ struct RowWorker {
         }
         ++passes;
         VC_CYC_INC(*this, kPDeg1Count);
+        if (any == 0u) {  // nothing to look at: pend stays empty
+            VC_CYC_ADD(*this, kPDeg1, t0);
+            return false;
+        }
         uint32_t prop[NW];
 #pragma unroll
         for (int w = 0; w < NW; ++w) prop[w] = 0u;
-        if (any == 0u) return finish(prop, kPDeg1, t0);
 #pragma unroll
         for (int k = 0; k < NW; ++k) {
             if (d1[k] == 0u) continue;
@@ -401,10 +430,13 @@ struct RowWorker {
         }
         ++passes;
         VC_CYC_INC(*this, kPTriCount);
+        if (any == 0u) {  // nothing to look at: pend stays empty
+            VC_CYC_ADD(*this, kPTri, t0);
+            return false;
+        }
         uint32_t prop[NW];
 #pragma unroll
         for (int w = 0; w < NW; ++w) prop[w] = 0u;
-        if (any == 0u) return finish(prop, kPTri, t0);
 #pragma unroll
         for (int k = 0; k < NW; ++k) {
             if (cand[k] == 0u) continue;
