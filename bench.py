@@ -16,6 +16,7 @@ Reported:
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import os
 import re
@@ -33,6 +34,8 @@ METRIC = "search-tree nodes/sec and solves/sec (p50/p99 latency) vs plain launch
 NUM_GRAPHS = 4096
 L2_FLUSH_BYTES = 256 << 20
 CPU_SAMPLE_GRAPHS = 256  # about 15 s of single-core oracle work
+SIZE_BINS = ((0, 128), (128, 400), (400, 1000), (1000, 3000))  # n ranges of the served latency breakdown
+                                                               # (the first is the server's bit-row class)
 PLAIN_SAMPLE_GRAPHS = 512
 # Kernels in one replay of the batch plan: worklist init, greedy bound, traversal, answer gather.
 KERNELS_PER_STEP = 4
@@ -55,9 +58,32 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline leg")
     ap.add_argument("--no-serve", action="store_true", help="skip the served-stream leg")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
-    ap.add_argument("--serve-seconds", type=float, default=5.0)
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--sweep", default="1000,2000,3000,4000", help="served rates of the sweep (empty: none)")
+    ap.add_argument("--sweep-seconds", type=float, default=10.0)
+    ap.add_argument("--plain-rate", type=float, default=1000.0, help="rate of the equal-load comparison")
+    ap.add_argument("--plain-seconds", type=float, default=15.0)
+    ap.add_argument("--burst", type=int, default=20000, help="requests of the server's capacity burst")
+    ap.add_argument("--no-configs", action="store_true", help="skip configurations 1-3")
+    ap.add_argument("--serve-workers", type=int, default=0,
+                    help="CSR-walk workers of the server (0: its default split of the SMs)")
+    ap.add_argument("--serve-csr-only", action="store_true", help="serve every request on CSR walks")
     ap.add_argument("--serve-only", action="store_true", help="run only the served-stream leg")
     return ap.parse_args()
+
+
+def sweep_rates(a) -> tuple:
+    return tuple(float(x) for x in a.sweep.split(",") if x.strip())
+
+
+def serve_config(vc, a):
+    """The server's configuration from the command line (None: the library's defaults)."""
+    kw = {}
+    if a.serve_workers > 0:
+        kw["num_workers"] = a.serve_workers
+    if a.serve_csr_only:
+        kw["bit_rows"] = -1
+    return vc.make_config(**kw) if kw else None
 
 
 def dist_env():
@@ -438,7 +464,10 @@ def run_ours(a):
         clocks = clk.summary()
         line["clocks"] = clocks
         if not a.no_serve and world == 1:
-            line["serving"] = serving_leg(vc, a.serve_rate, a.serve_seconds)
+            line["serving"] = serving_leg(vc, a.serve_rate, a.serve_seconds, sweep_rates(a), a.sweep_seconds,
+                                          a.plain_rate, a.plain_seconds, a.burst, config=serve_config(vc, a))
+        if not a.no_configs and world == 1:
+            line["configs"] = configs_leg(vc, dev, local, with_oracle=not a.no_cpu)
         if not a.no_cpu and world == 1:
             seeds = list(range(min(CPU_SAMPLE_GRAPHS, G)))
             secs = oracle_solves(seeds, 1)
@@ -479,79 +508,231 @@ def load_serve_pool():
     return pool, total
 
 
-def serving_leg(vc, rate_hz: float, duration_s: float, budget_gib: int = 64):
-    """Open-loop Poisson stream (seeded): each request picks a pool graph, is PVC with probability
-    0.7 (k = MVC-1 or MVC) else MVC.  Latency = completion seen by the host - scheduled arrival."""
+def served_requests(rate_hz: float, duration_s: float, pool: list):
+    """The seeded Poisson stream (seed 0): request i picks a pool graph with draw i of stream 2^40,
+    is PVC with probability 0.7 (k = MVC-1 or MVC) else MVC.  Every rate sees the same sequence of
+    requests; only the arrival times scale.  Items: (arrival_s, kind, k, pool entry, answer)."""
     from paper_2204_10402_gb300 import graphs as G
-    pool, total = load_serve_pool()
     stream = G.request_stream(rate_hz, duration_s, seed=0)
+    pick = G.uniform01(1 << 40, max(len(stream), 1))
     reqs = []
-    for i, r in enumerate(stream):
-        u = G.uniform01(1 << 40, 1, i)[0]
+    for r, u in zip(stream, pick):
         e = pool[min(int(u * len(pool)), len(pool) - 1)]
         k = e["mvc"] + r.k_offset if r.kind == 1 else 0
         want = e["mvc"] if r.kind == 0 else int(k >= e["mvc"])
         reqs.append((r.arrival_s, r.kind, k, e, want))
-    graphs = {}
-    for _, _, _, e, _ in reqs:
-        key = e["req"].seed
-        if key not in graphs:
-            graphs[key] = G.request_graph(e["req"])
-    max_n = max(g.n for g in graphs.values())
-    srv = vc.Server(max_n=max_n, budget_bytes=budget_gib << 30)
-    for key in list(graphs)[:32]:   # warm-up (module load, first launch)
-        srv.submit(graphs[key].offsets, graphs[key].neighbors, 0)
-    srv.drain(timeout_ms=600000)
+    return reqs
+
+
+def _percentiles(lat_ms) -> dict:
+    lat = np.asarray(lat_ms, dtype=np.float64)
+    if lat.size == 0:
+        return {"p50": None, "p99": None, "p999": None}
+    return {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+            "p999": float(np.percentile(lat, 99.9))}
+
+
+def run_served(srv, reqs, graphs, burst: bool = False) -> dict:
+    """Open loop: each request is submitted at its scheduled arrival (all at once with burst) and its
+    latency is the completion the host sees minus that arrival.  Records are released as read."""
+    st0 = srv.stats()
     ids = []
-    t0 = time.monotonic_ns() + 2_000_000
-    for arr, kind, k, e, want in reqs:
-        due = t0 + int(arr * 1e9)
-        while time.monotonic_ns() < due:
-            pass
-        g = graphs[e["req"].seed]
-        ids.append(srv.submit(g.offsets, g.neighbors, kind, k))
-    srv.drain(timeout_ms=600000)
-    infos = [srv.poll(i) for i in ids]
-    st = srv.stats()
-    srv.close()
-    lat = np.array([(x["done_ns"] - (t0 + int(r[0] * 1e9))) / 1e6 for x, r in zip(infos, reqs)])
+    gc.disable()  # a collector pause would delay submissions and show up as request latency
+    try:
+        t0 = time.monotonic_ns() + 2_000_000
+        for arr, kind, k, e, want in reqs:
+            due = t0 if burst else t0 + int(arr * 1e9)
+            while time.monotonic_ns() < due:
+                pass
+            g = graphs[e["req"].seed]
+            ids.append(srv.submit(g.offsets, g.neighbors, kind, k))
+        srv.drain(timeout_ms=900000)
+    finally:
+        gc.enable()
+    infos = [srv.poll(i, release=True) for i in ids]
+    st1 = srv.stats()
+    due = [t0 if burst else t0 + int(r[0] * 1e9) for r in reqs]
+    lat = [(x["done_ns"] - d) / 1e6 for x, d in zip(infos, due)]
+    lag = [(x["submit_ns"] - d) / 1e6 for x, d in zip(infos, due)]
     wrong = sum(1 for x, r in zip(infos, reqs) if x["answer"] != r[4] or x["status"] != 0)
-    span = (max(x["done_ns"] for x in infos) - t0) / 1e9
-    # Per-request plain launches on the same GPU: each request's service time measured with one
-    # synchronous vc_mvc / vc_pvc call (device-resident CSR), then the same arrivals replayed
-    # through a FIFO queue of one server.
+    span = (max(x["done_ns"] for x in infos) - t0) / 1e9 if infos else 0.0
+    sizes = [r[3]["req"].n for r in reqs]
+    bins = {}
+    for lo, hi in SIZE_BINS:
+        sel = [x for x, n in zip(lat, sizes) if lo < n <= hi]
+        bins[f"{lo + 1}-{hi}"] = {"requests": len(sel), **_percentiles(sel)}
+    return {"requests": len(reqs), "wrong_answers": wrong,
+            "solves_per_s": len(reqs) / span if span > 0 else None,
+            "latency_ms": _percentiles(lat),
+            "submit_lag_ms": _percentiles(lag),
+            "latency_ms_by_n": bins,
+            "launches": st1["launches"] - st0["launches"], "nodes_visited": st1["nodes_visited"] - st0["nodes_visited"],
+            "records_held_after": st1["records"]}
+
+
+def run_plain_open_loop(vc, reqs, dev_graphs) -> dict:
+    """Per-request plain launches, open loop: one host thread makes one synchronous vc_mvc / vc_pvc
+    call per request (device-resident CSR), starting at the request's arrival or, if the previous
+    call is still running, when it returns; latency = return - arrival."""
+    lat, wrong, busy = [], 0, 0.0
+    gc.disable()  # as in run_served: no collector pause inside the open loop
+    try:
+        t0 = time.monotonic_ns() + 2_000_000
+        for arr, kind, k, e, want in reqs:
+            due = t0 + int(arr * 1e9)
+            while time.monotonic_ns() < due:
+                pass
+            off, nbr = dev_graphs[e["req"].seed]
+            s = time.monotonic_ns()
+            a = vc.mvc(off, nbr, want_cover=False) if kind == 0 else vc.pvc(off, nbr, k, want_cover=False)
+            done = time.monotonic_ns()
+            busy += (done - s) / 1e9
+            lat.append((done - due) / 1e6)
+            wrong += int(a.value != want)
+        span = (time.monotonic_ns() - t0) / 1e9
+    finally:
+        gc.enable()
+    return {"requests": len(reqs), "wrong_answers": wrong, "solves_per_s": len(reqs) / span,
+            "latency_ms": _percentiles(lat), "capacity_solves_per_s": len(reqs) / busy if busy else None}
+
+
+def serving_leg(vc, rate_hz: float, duration_s: float, sweep_rates=(), sweep_s: float = 10.0,
+                plain_rate: float = 1000.0, plain_s: float = 15.0, burst: int = 20000, budget_gib: int = 64,
+                config=None):
+    """The served workload: the stream at rate_hz for duration_s, a rate sweep, the server's
+    capacity under a burst, and plain launches against the server at one rate both sustain."""
     import torch
-    dev_graphs = {key: (torch.from_numpy(g.offsets).cuda(), torch.from_numpy(g.neighbors if g.neighbors.size else np.zeros(1, np.int32)).cuda()) for key, g in graphs.items()}
-    sample = reqs[: min(len(reqs), 2000)]
-    service = []
-    for arr, kind, k, e, want in sample:
-        off, nbr = dev_graphs[e["req"].seed]
-        t = time.perf_counter()
-        if kind == 0:
-            vc.mvc(off, nbr, want_cover=False)
-        else:
-            vc.pvc(off, nbr, k, want_cover=False)
-        service.append(time.perf_counter() - t)
-    finish, plain_lat = 0.0, []
-    for (arr, *_), sv in zip(sample, service):
-        start = max(arr, finish)
-        finish = start + sv
-        plain_lat.append((finish - arr) * 1e3)
-    plain_lat = np.array(plain_lat)
-    return {
+    from paper_2204_10402_gb300 import graphs as G
+    pool, total = load_serve_pool()
+    graphs = {}
+    for e in pool:
+        graphs[e["req"].seed] = G.request_graph(e["req"])
+    max_n = max(g.n for g in graphs.values())
+    srv = vc.Server(max_n=max_n, budget_bytes=budget_gib << 30, config=config)
+    warm = served_requests(2000.0, 0.05, pool)
+    run_served(srv, warm, graphs, burst=True)  # module load, first launch
+    main = run_served(srv, served_requests(rate_hz, duration_s, pool), graphs)
+    out = {
         "workload": f"Poisson {rate_hz:g} req/s for {duration_s:g} s, 70% PVC (k = MVC-1 or MVC) / 30% MVC, "
                     f"graphs from a pool of {len(pool)} oracle-solved requests "
                     f"({total - len(pool)} of {total} candidates rejected over a 50K-node oracle cap)",
-        "requests": len(reqs), "wrong_answers": wrong,
-        "solves_per_s": len(reqs) / span,
-        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                       "p999": float(np.percentile(lat, 99.9))},
-        "plain_launches": {"sample": len(sample), "solves_per_s_capacity": len(sample) / sum(service),
-                           "latency_ms": {"p50": float(np.percentile(plain_lat, 50)),
-                                          "p99": float(np.percentile(plain_lat, 99)),
-                                          "p999": float(np.percentile(plain_lat, 99.9))}},
-        "server": {k: st[k] for k in ("launches", "epochs", "nodes_visited", "workers", "worker_threads")},
+        **main,
     }
+    st = srv.stats()
+    out["server"] = {k: st[k] for k in ("epochs", "workers", "worker_threads", "classes", "small_max_n",
+                                         "small_workers")}
+    if sweep_rates:
+        out["rate_sweep"] = []
+        for r in sweep_rates:
+            res = run_served(srv, served_requests(r, sweep_s, pool), graphs)
+            out["rate_sweep"].append({"offered_per_s": r, "seconds": sweep_s, **res})
+    if burst > 0:
+        reqs = served_requests(2000.0, burst / 2000.0 + 1.0, pool)[:burst]
+        res = run_served(srv, reqs, graphs, burst=True)
+        out["capacity_burst"] = {"requests": res["requests"], "solves_per_s": res["solves_per_s"],
+                                 "wrong_answers": res["wrong_answers"],
+                                 "note": "all requests submitted at once; completions per second of the span"}
+    if plain_rate > 0 and plain_s > 0:
+        reqs = served_requests(plain_rate, plain_s, pool)
+        served = run_served(srv, reqs, graphs)
+        dev_graphs = {key: (torch.from_numpy(g.offsets).cuda(),
+                            torch.from_numpy(g.neighbors if g.neighbors.size else np.zeros(1, np.int32)).cuda())
+                      for key, g in graphs.items()}
+        for key in list(dev_graphs)[:16]:  # warm-up of the plain path
+            vc.mvc(*dev_graphs[key], want_cover=False)
+        torch.cuda.synchronize()
+        plain = run_plain_open_loop(vc, reqs, dev_graphs)
+        out["equal_load"] = {"offered_per_s": plain_rate, "seconds": plain_s, "served": served,
+                             "plain_launches": plain,
+                             "note": "the same requests and arrival times through the server and through one "
+                                     "synchronous vc_mvc / vc_pvc call each (device-resident CSR)"}
+    srv.close()
+    return out
+
+
+def configs_leg(vc, dev, local: int, with_oracle: bool = True) -> dict:
+    """Configurations 1-3 of the workload set, each timed on the GPU (CUDA-synchronous calls through
+    the C ABI, device-resident CSR) with its answer checked, beside the single-core oracle."""
+    import torch
+
+    import oracle
+    from paper_2204_10402_gb300 import graphs as G
+    oracle.build()
+
+    def dev_csr(g):
+        return (torch.from_numpy(g.offsets).to(dev),
+                torch.from_numpy(g.neighbors if g.neighbors.size else np.zeros(1, np.int32)).to(dev))
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(reps):
+            t = time.perf_counter()
+            r = fn()
+            ms.append(1000 * (time.perf_counter() - t))
+        return r, ms
+
+    def oracle_ms(fn, reps):
+        ms = []
+        for _ in range(reps):
+            t = time.perf_counter()
+            r = fn()
+            ms.append(1000 * (time.perf_counter() - t))
+        return r, statistics.median(ms)
+
+    out = {}
+    with ClockSampler(local) as clk:
+        # 1: MVC of G(60, 0.10), seed 0, with a verified cover; a single request.
+        g1 = G.gnp(60, 0.10, 0)
+        want1 = oracle.mvc(g1)[0]
+        off, nbr = dev_csr(g1)
+        a1, ms1 = timed(lambda: vc.mvc(off, nbr), 200)
+        cover = a1.cover.cpu().numpy().astype(bool)
+        _, ms1h = timed(lambda: vc.mvc(g1.offsets, g1.neighbors), 50)
+        out["config1"] = {"workload": "MVC of G(60, 0.10), seed 0, one request", "mvc": a1.value,
+                          "correct": a1.value == want1 and int(cover.sum()) == a1.value and oracle.verify_cover(g1, cover),
+                          "latency_ms": {"p50": statistics.median(ms1), "p99": float(np.percentile(ms1, 99))},
+                          "latency_host_arrays_ms_p50": statistics.median(ms1h), "nodes": a1.stats["nodes_visited"]}
+        # 2: PVC on Chung-Lu n=2000 (avg degree 6, exponent 2.5, cap 200), seed 0, k = MVC and MVC-1.
+        g2 = G.chung_lu(2000, 6.0, 0)
+        mvc2 = oracle.mvc(g2)[0]
+        off, nbr = dev_csr(g2)
+        c2 = {"workload": "PVC of Chung-Lu n=2000 (average degree 6, exponent 2.5, cap 200), seed 0", "mvc": mvc2}
+        for name, k, want in (("k_mvc", mvc2, 1), ("k_mvc_minus_1", mvc2 - 1, 0)):
+            a2, ms2 = timed(lambda: vc.pvc(off, nbr, k), 50)
+            c2[name] = {"k": k, "found": a2.value, "correct": a2.value == want,
+                        "latency_ms": {"p50": statistics.median(ms2), "p99": float(np.percentile(ms2, 99))},
+                        "nodes": a2.stats["nodes_visited"]}
+        out["config2"] = c2
+        # 3: the largest member of the G(n, 0.05) + planted K_{25n/400} family that finishes: n = 200
+        # (n = 400 is intractable for this method), 32- and 16-bit degree arrays.
+        gold = {int(l.split()[0]): l.split() for l in open(os.path.join(ROOT, "tests", "golden", "planted_clique_mvc.txt"))
+                if not l.startswith("#")}
+        g3, _ = G.gnp_with_planted_clique(200, 0.05, 12, 0)
+        off, nbr = dev_csr(g3)
+        c3 = {"workload": "MVC of G(200, 0.05) + planted K_12, seed 0 (the n = 400 member is intractable)",
+              "mvc_oracle_stored": int(gold[200][3])}
+        for width in (32, 16):
+            cfg = vc.make_config(width=width)
+            a3, ms3 = timed(lambda: vc.mvc(off, nbr, config=cfg, want_cover=False), 2)
+            c3[f"int{width}"] = {"mvc": a3.value, "correct": a3.value == int(gold[200][3]),
+                                 "ms": min(ms3), "kernel_ms": a3.stats["kernel_ms"], "nodes": a3.stats["nodes_visited"],
+                                 "nodes_per_s": a3.stats["nodes_visited"] / (a3.stats["kernel_ms"] * 1e-3)}
+        out["config3"] = c3
+    out["clocks"] = clk.summary()
+    if with_oracle:
+        _, o1 = oracle_ms(lambda: oracle.mvc(g1), 5)
+        out["config1"]["oracle_1core_ms"] = o1
+        _, o2 = oracle_ms(lambda: oracle.pvc(g2, mvc2 - 1), 5)
+        out["config2"]["oracle_1core_ms_k_mvc_minus_1"] = o2
+        g160, _ = G.gnp_with_planted_clique(160, 0.05, 10, 0)
+        r160, o3 = oracle_ms(lambda: oracle.mvc(g160), 1)
+        out["config3"]["oracle_1core"] = {
+            "n160_ms": o3, "n160_nodes": r160[2]["nodes"],
+            "n200_s_stored": float(gold[200][5]), "n200_nodes_stored": int(gold[200][4]),
+            "note": "n = 160 timed in this run; n = 200 from tests/golden/planted_clique_mvc.txt (another host)"}
+    return out
 
 
 def plain_launches(vc, b, dev, stream, batched_value):
@@ -584,7 +765,8 @@ def main():
         from paper_2204_10402_gb300 import build
         build.build()
         vc.load()
-        print(json.dumps(serving_leg(vc, a.serve_rate, a.serve_seconds)), flush=True)
+        print(json.dumps(serving_leg(vc, a.serve_rate, a.serve_seconds, sweep_rates(a), a.sweep_seconds,
+                                     a.plain_rate, a.plain_seconds, a.burst, config=serve_config(vc, a))), flush=True)
         return
     if a.impl == "reference":
         run_reference(a)
