@@ -16,6 +16,9 @@ struct Launchers {
     int (*reduce)(int wt, int smem, cudaStream_t s, const ReduceParams &R);
     // Resident blocks per SM of the traversal kernel at this worker size and shared memory.
     int (*occupancy)(int wt, int smem, int *blocks_per_sm);
+    // The same for the serving instance, which this also loads and configures (so that its first
+    // launch loads no code while another persistent launch is running).
+    int (*serve_prepare)(int wt, int smem, int *blocks_per_sm);
 };
 
 const Launchers &launchers_w16();

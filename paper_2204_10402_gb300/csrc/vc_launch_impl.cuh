@@ -17,6 +17,19 @@ static int prepare(Kernel k, int smem) {
     return VC_OK;
 }
 
+// The server's launches (one per size class) run side by side on the same SMs.  An SM changes its
+// shared-memory / L1 split only while idle, so both instances ask for the same split -- all of the
+// configurable memory as shared memory -- and the blocks of one never wait for the other's to leave
+// an SM that was configured with a smaller shared-memory share.
+template <typename Kernel>
+static int prepare_serving(Kernel k, int smem) {
+    if (int rc = prepare(k, smem)) return rc;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared) !=
+        cudaSuccess)
+        return VC_ECUDA;
+    return VC_OK;
+}
+
 static inline int launch_status() { return cudaPeekAtLastError() == cudaSuccess ? VC_OK : VC_ECUDA; }
 
 // Runs the statement with constexpr WT bound to the worker size; bit-row kernels exist for
@@ -51,7 +64,7 @@ struct LaunchImpl {
                 return VC_EINVAL;
             } else {
                 VC_WT_SWITCH(wt, {
-                    if (int rc = prepare(traverse_kernel<W, WT, GM, NW, true>, smem)) return rc;
+                    if (int rc = prepare_serving(traverse_kernel<W, WT, GM, NW, true>, smem)) return rc;
                     traverse_kernel<W, WT, GM, NW, true><<<grid, WT, smem, s>>>(P);
                 });
                 return launch_status();
@@ -79,8 +92,21 @@ struct LaunchImpl {
         });
         return VC_OK;
     }
+    static int serve_prepare(int wt, int smem, int *blocks) {
+        if constexpr (GM || (NW != 0 && NW != 4)) {
+            return VC_EINVAL;
+        } else {
+            VC_WT_SWITCH(wt, {
+                if (int rc = prepare_serving(traverse_kernel<W, WT, GM, NW, true>, smem)) return rc;
+                if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, traverse_kernel<W, WT, GM, NW, true>, WT, smem) !=
+                    cudaSuccess)
+                    return VC_ECUDA;
+            });
+            return VC_OK;
+        }
+    }
     static const Launchers &table() {
-        static const Launchers L = {&greedy, &traverse, &reduce, &occupancy};
+        static const Launchers L = {&greedy, &traverse, &reduce, &occupancy, &serve_prepare};
         return L;
     }
 };

@@ -7,8 +7,8 @@
 //   lane 0  graphs of at most 128 vertices: one-warp bit-row workers (node in registers)
 //   lane 1  larger graphs: CSR-walk workers sized for the server's max_n
 // (One lane only when max_n <= 128, or when the configuration asks for CSR walks.)  The two
-// launches run side by side on their own streams, each with half of every SM's thread slots, and
-// never wait on one another.  Stacks and worklist of a lane are sized for its largest graph.
+// launches run side by side on their own streams, lane 1 with three quarters of every SM's thread
+// slots and lane 0 with the rest, and never wait on one another.  Stacks and worklist of a lane are sized for its largest graph.
 //
 // A host thread owned by the server, for every lane:
 //   - admits queued requests while their bytes fit: each request reserves a slot and a range of
@@ -47,6 +47,7 @@ constexpr size_t kAlign = 128;
 constexpr int32_t kSmallN = 128;      // largest graph of the bit-row lane
 constexpr int kSmallRowWords = 4;     // its bit rows: 4 words per vertex (n <= 128)
 constexpr int kMaxLanes = 2;
+constexpr int kThreadSlotsPerSm = 1024;  // threads an SM holds at the traversal's 64 registers
 
 int64_t now_ns() {
     return std::chrono::duration_cast<std::chrono::nanoseconds>(
@@ -139,6 +140,10 @@ Problem *stage_problem(Lane &L, int32_t slot) {
 uint32_t *stage_ring(Lane &L) { return reinterpret_cast<uint32_t *>(L.stage_h + (size_t)L.slots * kSlotStride); }
 uint32_t *stage_tail(Lane &L) { return stage_ring(L) + L.slots; }
 int32_t *stage_flags(Lane &L) { return reinterpret_cast<int32_t *>(stage_tail(L) + L.slots + 1); }
+// Pinned zeros (the size of the control block) that the lane copies over the words it resets.
+// Resets are copies rather than memsets: a memset may run a kernel the driver loads on first use,
+// and loading code can wait for every running launch, such as the other lane's persistent one.
+const void *stage_zeros(Lane &L) { return L.stage_h + (size_t)L.slots * kSlotStride + sizeof(uint32_t) * (2 * (size_t)L.slots + 1) + 64; }
 
 Params serve_params(const vc_server *s, const Lane &L) {
     Params P;
@@ -178,8 +183,10 @@ const Launchers &lane_launchers(const Lane &L) { return launchers(L.width, false
 // Launches the lane's persistent traversal (the server lock is held).
 int launch(vc_server *s, Lane &L) {
     const Launchers &LL = lane_launchers(L);
-    if (cudaMemsetAsync(L.ctrl, 0, sizeof(Control), L.kstream) != cudaSuccess) return VC_ECUDA;
-    if (cudaMemsetAsync(L.close_now, 0, sizeof(int32_t), L.kstream) != cudaSuccess) return VC_ECUDA;
+    if (cudaMemcpyAsync(L.ctrl, stage_zeros(L), sizeof(Control), cudaMemcpyHostToDevice, L.kstream) != cudaSuccess)
+        return VC_ECUDA;
+    if (cudaMemcpyAsync(L.close_now, stage_zeros(L), sizeof(int32_t), cudaMemcpyHostToDevice, L.kstream) != cudaSuccess)
+        return VC_ECUDA;
     Params P = serve_params(s, L);
     if (int rc = launch_init_worklist(L.wl_seq, L.cap, L.ctrl, L.kstream, L.claim_state)) return rc;
     if (int rc = LL.traverse(L.wt, L.workers, L.smem, L.kstream, P)) return rc;
@@ -296,8 +303,9 @@ int reset_epoch(Lane &L) {
     L.published = 0;
     L.draining = false;
     L.epochs++;
-    if (cudaMemsetAsync(L.claim_state, 0, sizeof(unsigned long long), L.cstream) != cudaSuccess ||
-        cudaMemsetAsync(L.sub_tail, 0, sizeof(uint32_t), L.cstream) != cudaSuccess ||
+    if (cudaMemcpyAsync(L.claim_state, stage_zeros(L), sizeof(unsigned long long), cudaMemcpyHostToDevice,
+                        L.cstream) != cudaSuccess ||
+        cudaMemcpyAsync(L.sub_tail, stage_zeros(L), sizeof(uint32_t), cudaMemcpyHostToDevice, L.cstream) != cudaSuccess ||
         cudaStreamSynchronize(L.cstream) != cudaSuccess)
         return VC_ECUDA;
     return VC_OK;
@@ -428,12 +436,14 @@ int make_lane(const vc_server *s, Lane &L, const cudaDeviceProp &prop, size_t bu
     }
     L.smem = smem_bytes_for(L.max_n, L.width / 8, L.csr_words, L.nw);
     if (L.smem > (int)prop.sharedMemPerBlockOptin) return VC_EINVAL;
+    // Loads and configures the lane's kernel now: a kernel loaded on its first launch may wait for
+    // every running launch to finish, and the other lane's persistent launch could be one.
     int per_sm = 0;
-    if (lane_launchers(L).occupancy(L.wt, L.smem, &per_sm) != VC_OK || per_sm <= 0) return VC_EINVAL;
+    if (lane_launchers(L).serve_prepare(L.wt, L.smem, &per_sm) != VC_OK || per_sm <= 0) return VC_EINVAL;
     per_sm = std::max(1, (int)((float)per_sm * share));
     L.eb = entry_bytes_for(L.max_n, L.width / 8);
     L.depth = L.max_n + 3;  // MVC depth <= n + 1, PVC depth <= min(k, n) + 2
-    L.slots = 4096;
+    L.slots = 16384;
     // Worklist: the batch default of the size class, limited to an eighth of the lane's budget.
     L.cap = default_worklist_capacity(L.eb, tuned.capacity);
     while (L.cap > 1024 && (size_t)L.cap * (size_t)L.eb > budget / 8) L.cap >>= 1;
@@ -490,7 +500,8 @@ int make_lane(const vc_server *s, Lane &L, const cudaDeviceProp &prop, size_t bu
     L.arena = b + o_arena;
     L.rows = L.nw > 0 ? reinterpret_cast<uint32_t *>(b + o_rows) : nullptr;
     L.stacks = b + o_stacks;
-    const size_t stage_bytes = (size_t)L.slots * kSlotStride + sizeof(uint32_t) * (2 * (size_t)L.slots + 1) + 64;
+    const size_t stage_bytes =
+        (size_t)L.slots * kSlotStride + sizeof(uint32_t) * (2 * (size_t)L.slots + 1) + 64 + sizeof(Control);
     if (cudaMemset(L.mem, 0, o_arena) != cudaSuccess ||
         cudaHostAlloc(reinterpret_cast<void **>(&L.completion_h), sizeof(int32_t) * 4 * (size_t)L.slots,
                       cudaHostAllocMapped) != cudaSuccess ||
@@ -503,6 +514,13 @@ int make_lane(const vc_server *s, Lane &L, const cudaDeviceProp &prop, size_t bu
         return VC_ENOMEM;
     }
     std::memset(L.completion_h, 0, sizeof(int32_t) * 4 * (size_t)L.slots);
+    std::memset(L.stage_h, 0, stage_bytes);
+    // The worklist initialiser too (it runs before every launch of the lane).
+    if (launch_init_worklist(L.wl_seq, L.cap, L.ctrl, L.kstream, L.claim_state) != VC_OK ||
+        cudaStreamSynchronize(L.kstream) != cudaSuccess) {
+        cudaGetLastError();
+        return VC_ECUDA;
+    }
     return VC_OK;
 }
 
@@ -554,17 +572,31 @@ int vc_server_create(const vc_config *cfg, size_t device_bytes_budget, int32_t m
     const bool large = !small || max_n > kSmallN;
     const bool both = small && large;
     int rc = VC_OK;
+    // With two classes the CSR-walk class takes cfg->num_workers workers if given (else three
+    // quarters of every SM's thread slots) and the bit-row class the slots that remain.
+    float small_share = both ? 0.25f : 1.f, large_share = both ? 0.75f : 1.f;
+    if (both && s->cfg.num_workers > 0) {
+        const int wt = s->cfg.worker_threads ? s->cfg.worker_threads : tuned_defaults(max_n).worker_threads;
+        const int64_t per_sm = (s->cfg.num_workers + prop.multiProcessorCount - 1) / prop.multiProcessorCount;
+        const float used = (float)(per_sm * wt) / (float)kThreadSlotsPerSm;
+        if (used >= 1.f) {
+            delete s;
+            return VC_EINVAL;  // no room left for the bit-row class
+        }
+        large_share = 1.f;  // the worker count itself is the limit
+        small_share = 1.f - used;
+    }
     if (small) {
         Lane &L = s->lane[s->nlanes++];
         L.max_n = std::min(max_n, kSmallN);
         L.nw = kSmallRowWords;
-        rc = make_lane(s, L, prop, both ? s->budget / 8 : s->budget, both ? 0.5f : 1.f);
+        rc = make_lane(s, L, prop, both ? s->budget / 8 : s->budget, small_share);
     }
     if (rc == VC_OK && large) {
         Lane &L = s->lane[s->nlanes++];
         L.max_n = max_n;
         L.nw = 0;
-        rc = make_lane(s, L, prop, both ? s->budget - s->budget / 8 : s->budget, both ? 0.5f : 1.f);
+        rc = make_lane(s, L, prop, both ? s->budget - s->budget / 8 : s->budget, large_share);
     }
     if (rc != VC_OK) {
         for (int i = 0; i < s->nlanes; ++i) free_lane(s->lane[i]);
