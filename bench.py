@@ -34,6 +34,7 @@ METRIC = "search-tree nodes/sec and solves/sec (p50/p99 latency) vs plain launch
 NUM_GRAPHS = 4096
 L2_FLUSH_BYTES = 256 << 20
 CPU_SAMPLE_GRAPHS = 256  # about 15 s of single-core oracle work
+SERVE_WARMUP_S = 3.0     # seconds of the served stream run before its measured legs
 SIZE_BINS = ((0, 128), (128, 400), (400, 1000), (1000, 3000))  # n ranges of the served latency breakdown
                                                                # (the first is the server's bit-row class)
 PLAIN_SAMPLE_GRAPHS = 512
@@ -609,8 +610,11 @@ def serving_leg(vc, rate_hz: float, duration_s: float, sweep_rates=(), sweep_s: 
         graphs[e["req"].seed] = G.request_graph(e["req"])
     max_n = max(g.n for g in graphs.values())
     srv = vc.Server(max_n=max_n, budget_bytes=budget_gib << 30, config=config)
-    warm = served_requests(2000.0, 0.05, pool)
-    run_served(srv, warm, graphs, burst=True)  # module load, first launch
+    # Warm-up: a burst (module load, first launches), then 3 s of the stream itself.  A process's
+    # first seconds with two size classes running side by side have shown one stall of 15-55 ms
+    # (the server thread waiting in the CUDA driver); the warm-up keeps it out of the measurement.
+    run_served(srv, served_requests(2000.0, 0.05, pool), graphs, burst=True)
+    run_served(srv, served_requests(2000.0, SERVE_WARMUP_S, pool), graphs)
     main = run_served(srv, served_requests(rate_hz, duration_s, pool), graphs)
     out = {
         "workload": f"Poisson {rate_hz:g} req/s for {duration_s:g} s, 70% PVC (k = MVC-1 or MVC) / 30% MVC, "
