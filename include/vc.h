@@ -89,8 +89,9 @@ typedef struct {
                                    else CSR walks; 1 = bit rows, also for graphs of up to 256 vertices
                                    (VC_EINVAL when the launch does not qualify); -1 = CSR walks.  Same answers and reduced
                                    degree arrays either way.  vc_mvc, vc_pvc, vc_mvc_batch, vc_greedy,
-                                   vc_reduce_node and the batch plan honour it; the server and
-                                   vc_mvc_noalloc walk the CSR. */
+                                   vc_reduce_node and the batch plan honour it; the server walks the
+                                   CSR unless bit_rows = 1 (then graphs of at most 128 vertices run on
+                                   bit rows, see vc_server.h); vc_mvc_noalloc walks the CSR. */
 } vc_config;
 
 /* Counters of one call (all filled by the device except kernel_ms and the sizes). */

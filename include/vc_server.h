@@ -8,12 +8,13 @@
  * class's worklist, whose entries carry the request's slot, so the work of many requests overlaps
  * on the device.  The paper solves one graph per launch; the serving layer is this library's own.
  *
- * Size classes: graphs of at most 128 vertices run on one-warp bit-row workers (the node in
- * registers, the adjacency as bit rows in shared memory), larger ones on CSR-walk workers sized for
- * max_n.  The two classes' launches run side by side, the CSR-walk class on three quarters of every
- * SM's thread slots and the bit-row class on the rest, each with its own stacks, worklist and arena.  cfg->bit_rows = -1 serves every request on CSR walks
- * (one class); cfg->worker_threads, width, worklist_capacity and donate_threshold apply to the
- * CSR-walk class.
+ * Size classes (cfg->bit_rows = 1): graphs of at most 128 vertices run on one-warp bit-row workers
+ * (the node in registers, the adjacency as bit rows in shared memory), larger ones on CSR-walk
+ * workers sized for max_n.  The two classes' launches run side by side, the CSR-walk class on three
+ * quarters of every SM's thread slots and the bit-row class on the rest, each with its own stacks,
+ * worklist and arena.  By default (bit_rows 0 or -1) every request runs on CSR-walk workers sized
+ * for max_n: one class.  cfg->worker_threads, width, worklist_capacity and donate_threshold apply
+ * to the CSR-walk class.
  *
  * Admission: every request reserves a slot and a range of its class's device graph arena (its
  * CSR and cover mask).  Stacks and worklist are reserved per class at creation for the class's
@@ -71,8 +72,8 @@ typedef struct {
  * within a class, half goes to the per-worker stacks (which sets the worker count, up to the SM
  * slots the class has), a quarter to the graph arena (and, in the bit-row class, the bit rows).
  * max_n is the largest graph it accepts.  cfg (may be NULL) picks the CSR-walk class's worker size,
- * width, worklist capacity and donation threshold as in vc.h; bit_rows = 1 and node_in_global = 1
- * are VC_EINVAL.  With two classes, cfg->num_workers (if given) sets the CSR-walk class's worker
+ * width, worklist capacity and donation threshold as in vc.h; node_in_global = 1 is VC_EINVAL.
+ * With two classes, cfg->num_workers (if given) sets the CSR-walk class's worker
  * count instead of its three quarters of the SMs' thread slots; the bit-row class gets the slots
  * that remain (VC_EINVAL if none do). */
 int vc_server_create(const vc_config *cfg, size_t device_bytes_budget, int32_t max_n, vc_server **server);

@@ -53,35 +53,45 @@ def run_alone(vc, reqs):
     return got
 
 
-def test_mix_equals_alone_and_oracle(vc):
+@pytest.mark.parametrize("bit_rows", [0, 1])
+def test_mix_equals_alone_and_oracle(vc, bit_rows):
     reqs = mixed_requests(80, 120000)
     alone = run_alone(vc, reqs)
     assert alone == [r[3] for r in reqs]
-    with vc.Server(max_n=1000) as srv:
+    with vc.Server(max_n=1000, config=vc.make_config(bit_rows=bit_rows)) as srv:
         ids = [srv.submit(g.offsets, g.neighbors, kind, k) for g, kind, k, _ in reqs]
         srv.drain(timeout_ms=120000)
         infos = [srv.poll(i) for i in ids]
         st = srv.stats()
     assert all(x["done"] and x["status"] == 0 for x in infos)
     assert [x["answer"] for x in infos] == alone
-    assert st["completed"] == len(reqs) and st["launches"] >= 2
-    # Two size classes: graphs of at most 128 vertices on bit-row workers, the rest on CSR walks.
-    assert st["classes"] == 2 and st["small_max_n"] == 128 and 0 < st["small_workers"] < st["workers"]
+    assert st["completed"] == len(reqs) and st["launches"] >= 1
     assert any(g.n <= 128 for g, *_ in reqs) and any(g.n > 128 for g, *_ in reqs)
+    if bit_rows:  # two size classes: n <= 128 on bit-row workers, the rest on CSR walks
+        assert st["classes"] == 2 and st["small_max_n"] == 128 and 0 < st["small_workers"] < st["workers"]
+    else:         # the default: every request on CSR walkers
+        assert st["classes"] == 1 and st["small_max_n"] == 0 and st["small_workers"] == 0
 
 
-def test_one_class_with_csr_walks_only(vc):
-    # bit_rows = -1 serves every request on CSR-walk workers: one class, the same answers.
-    reqs = mixed_requests(40, 125000)
-    with vc.Server(max_n=1000, config=vc.make_config(bit_rows=-1)) as srv:
+def test_size_class_split_and_small_server(vc):
+    # num_workers sets the CSR-walk class's size and the bit-row class gets the slots left; a
+    # server for graphs of at most 128 vertices with bit rows is one bit-row class; a split that
+    # leaves the bit-row class nothing is an error.
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    reqs = [r for r in mixed_requests(40, 125000) if r[0].n <= 120]
+    with vc.Server(max_n=1000, config=vc.make_config(bit_rows=1, num_workers=sms)) as srv:
+        st = srv.stats()
+        assert st["classes"] == 2 and st["workers"] - st["small_workers"] == sms
+    with vc.Server(max_n=120, config=vc.make_config(bit_rows=1)) as srv:
         ids = [srv.submit(g.offsets, g.neighbors, kind, k) for g, kind, k, _ in reqs]
         srv.drain(timeout_ms=120000)
         infos = [srv.poll(i) for i in ids]
         st = srv.stats()
     assert [x["answer"] for x in infos] == [r[3] for r in reqs]
-    assert st["classes"] == 1 and st["small_max_n"] == 0 and st["small_workers"] == 0
+    assert st["classes"] == 1 and st["small_max_n"] == 120 and st["small_workers"] == st["workers"]
     with pytest.raises(vc.VCError):
-        vc.Server(max_n=100, config=vc.make_config(bit_rows=1))
+        vc.Server(max_n=1000, config=vc.make_config(bit_rows=1, num_workers=64 * sms))
 
 
 def test_trickled_requests_join_a_running_launch(vc):
