@@ -17,9 +17,9 @@
  * to the CSR-walk class.
  *
  * Admission: every request reserves a slot and a range of its class's device graph arena (its
- * CSR and cover mask).  Stacks and worklist are reserved per class at creation for the class's
- * largest graph (depth n + 3 entries of the degree-array size per worker, n = 128 or max_n), so
- * any accepted request fits them.  A request whose bytes do not fit the arena right now waits in a
+ * CSR, its cover mask and one entry for its reduced root node).  Stacks and worklist are reserved
+ * per class at creation for the class's largest graph (depth n + 3 entries of the degree-array
+ * size per worker, n = 128 or max_n), so any accepted request fits them.  A request whose bytes do not fit the arena right now waits in a
  * host queue and is admitted when earlier requests of its class finish; it is never refused for
  * lack of room unless it alone is larger than the whole arena.
  *

@@ -34,7 +34,7 @@ struct Workspace {
     int device = -1;
     int sms = 0;
     int smem_optin = 0;
-    DevBuf csr_off, csr_adj, problems, adj_len, ctrl, cover, stacks, wl_slots, wl_seq, sm_nodes, gstate, rows;
+    DevBuf csr_off, csr_adj, problems, adj_len, ctrl, cover, stacks, wl_slots, wl_seq, sm_nodes, gstate, rows, roots;
     void *pinned = nullptr;
     size_t pinned_cap = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -114,7 +114,7 @@ int workspace(Workspace **out) {
 
 void free_workspace(Workspace &ws) {
     DevBuf *bufs[] = {&ws.csr_off, &ws.csr_adj, &ws.problems, &ws.adj_len, &ws.ctrl, &ws.cover,
-                      &ws.stacks, &ws.wl_slots, &ws.wl_seq, &ws.sm_nodes, &ws.gstate, &ws.rows};
+                      &ws.stacks, &ws.wl_slots, &ws.wl_seq, &ws.sm_nodes, &ws.gstate, &ws.rows, &ws.roots};
     for (DevBuf *b : bufs) {
         if (b->p) cudaFree(b->p);
         b->p = nullptr;
@@ -266,6 +266,7 @@ int run(Workspace &ws, const Spec &spec, const vc_config *cfg_in, cudaStream_t s
     int64_t *h_adj_len = reinterpret_cast<int64_t *>(static_cast<uint8_t *>(ws.pinned) + adj_len_at);
     Control *h_ctrl = reinterpret_cast<Control *>(static_cast<uint8_t *>(ws.pinned) + ctrl_at);
     std::memcpy(h_probs, spec.probs.data(), sizeof(Problem) * (size_t)G);
+    for (int g = 0; g < G; ++g) h_probs[g].root_base = (int64_t)g * eb;  // one root entry per problem
     std::memcpy(h_adj_len, spec.adj_len.data(), sizeof(int64_t) * (size_t)G);
 
     const int32_t *d_off = spec.offsets, *d_adj = spec.neighbors;
@@ -311,6 +312,9 @@ int run(Workspace &ws, const Spec &spec, const vc_config *cfg_in, cudaStream_t s
         VC_RC(grow(ws.rows, sizeof(uint32_t) * (size_t)nw * (size_t)std::max<int64_t>(spec.total_vertices, 1)));
         P.rows = static_cast<uint32_t *>(ws.rows.p);
     }
+    // The greedy pass keeps each problem's first fixpoint here as its root node.
+    VC_RC(grow(ws.roots, (size_t)G * (size_t)eb));
+    P.roots = static_cast<uint8_t *>(ws.roots.p);
 
     if (!cfg.skip_validation)
         VC_RC(launch_validate(d_off, d_adj, d_probs, static_cast<const int64_t *>(ws.adj_len.p), G,

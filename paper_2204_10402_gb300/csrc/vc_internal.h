@@ -55,6 +55,7 @@ struct alignas(128) Problem {
     int32_t units;       // work units alive: unclaimed root + worklist entries + workers holding work
     int32_t done;        // 1 once the last unit was released
     int32_t tag;         // serving: completion tag the host waits for (0 otherwise)
+    int64_t root_base;   // byte offset of this problem's root entry in Params::roots
 };
 
 // Launch-wide control block.  Words that many workers hit with atomics or polls each own a
@@ -105,6 +106,8 @@ struct Params {
     int32_t gstate_bytes;
     uint32_t *rows;          // bit-row kernels: NW words per vertex, at cover_base * NW per problem
                              // (written by the greedy pass); null = each worker builds its own
+    uint8_t *roots;          // one entry (entry_bytes) per problem at its root_base: the root node
+                             // reduced by the greedy pass's first fixpoint; null = roots from the CSR
     int64_t idle_timeout_ns;
     const volatile int32_t *cancel;
     unsigned long long *sm_nodes;  // per-SM node counters

@@ -54,6 +54,19 @@ __device__ __forceinline__ uint32_t *rows_of(const Params &P, const Ctx &c) {
     else return P.rows ? P.rows + (size_t)(c.cover - P.cover) * NW : nullptr;
 }
 
+// A problem's root entry (Params::roots), written by the greedy pass.
+__device__ __forceinline__ uint8_t *root_entry(const Params &P, int32_t p) {
+    return P.roots + __ldcg(&P.problems[p].root_base);
+}
+
+// The root node of problem p: the greedy pass's first fixpoint when it was kept, else the whole
+// graph from the CSR.
+template <class Wk>
+__device__ __forceinline__ void load_root_node(const Params &P, Wk &w, int32_t p) {
+    if (P.roots) w.load_entry(root_entry(P, p), P.entry_bytes, P.n_max);
+    else w.load_root(make_ctx(P, p));
+}
+
 template <class Wk>
 __device__ bool greedy_solve(const Params &P, Wk &w, Ctx &c) {
     w.cur_n = c.n;
@@ -70,8 +83,14 @@ __device__ bool greedy_solve(const Params &P, Wk &w, Ctx &c) {
     w.stage(c, rows_of<Wk::kRowWords>(P, c));
     w.load_root(c);
     const int32_t m0 = w.node_m();
-    for (;;) {
+    for (bool first = true;; first = false) {
         reduce_fixpoint(w, c, 0, kRuleDeg1 | kRuleDeg2Tri, false);
+        // The first fixpoint is the root node with its degree-one and triangle vertices in S: the
+        // traversal starts from it instead of reducing the whole graph again (reading R13).
+        if (first && P.roots) {
+            w.store_entry(root_entry(P, c.index), P.entry_bytes, -1);
+            w.sync();
+        }
         if (w.node_m() == 0) break;
         int dv;
         const int v = w.argmax(c, dv);
@@ -366,7 +385,7 @@ __device__ int acquire(const Params &P, Wk &w) {
     const int arg = w.sc[kScB5];
     if (result == 1) {
         VC_CHECK(ctrl, arg >= 0 && arg < P.num_problems, 12, arg, return 0);
-        w.load_root(make_ctx(P, arg));
+        load_root_node(P, w, arg);
     } else if (result == 3) {
         VC_CHECK(ctrl, arg >= 0 && arg < P.num_problems, 18, arg, return 0);
     } else if (result == 2) {
@@ -450,7 +469,8 @@ __global__ void __launch_bounds__(kMaxThreads(WT), kMinBlocks(WT)) traverse_kern
                     c = make_ctx(P, cur);
                     VC_CHECK(ctrl, c.n >= 0 && c.n <= P.n_max, 19, c.n, { stop = true; break; });
                     if (!greedy_solve(P, w, c)) continue;  // answered by the greedy bound: release
-                    w.load_root(c);
+                    load_root_node(P, w, cur);
+                    w.node_loaded(c);
                 }
             } else {
                 cur = w.node_problem();

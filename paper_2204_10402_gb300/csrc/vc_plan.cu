@@ -143,6 +143,8 @@ int vc_plan_create_mvc_batch(int32_t G, const int32_t *vtx, const int32_t *edge,
     const size_t o_wl = take((size_t)cap * pl->eb);
     const size_t o_stk = take((size_t)pl->workers * (size_t)depth * pl->eb);
     const size_t o_rows = take(sizeof(uint32_t) * (size_t)pl->nw * (size_t)std::max<int64_t>(total_v, 1));
+    const size_t o_roots = take((size_t)G * pl->eb);  // each problem's root node, kept by the greedy pass
+    for (int g = 0; g < G; ++g) probs[g].root_base = (int64_t)g * pl->eb;
     if (cudaMalloc(&pl->mem, off) != cudaSuccess) {
         cudaGetLastError();
         delete pl;
@@ -197,6 +199,7 @@ int vc_plan_create_mvc_batch(int32_t G, const int32_t *vtx, const int32_t *edge,
     P.cancel = cfg.cancel;
     P.sm_nodes = reinterpret_cast<unsigned long long *>(b + o_smn);
     P.rows = pl->nw > 0 ? reinterpret_cast<uint32_t *>(b + o_rows) : nullptr;
+    P.roots = b + o_roots;
     if (rc == VC_OK && (cudaEventCreate(&pl->ev0) != cudaSuccess || cudaEventCreate(&pl->ev1) != cudaSuccess)) rc = VC_ECUDA;
     if (rc == VC_OK && cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) rc = VC_ECUDA;
     if (rc == VC_OK) {

@@ -13,7 +13,7 @@
 //
 // A host thread owned by the server, for every lane:
 //   - admits queued requests while their bytes fit: each request reserves a slot and a range of
-//     its lane's graph arena (CSR + cover mask);
+//     its lane's graph arena (CSR, cover mask and root entry);
 //   - uploads the request on the lane's copy stream (CSR, slot record, ring entry, then the ring
 //     tail, all ordered on that stream) while the launch keeps running;
 //   - harvests completion records that the device writes into host-mapped memory;
@@ -165,6 +165,7 @@ Params serve_params(const vc_server *s, const Lane &L) {
     P.wl_threshold = L.threshold;
     P.csr_words = L.csr_words;
     P.rows = L.rows;  // bit-row lane: rows at cover_base * nw words, written by each request's greedy pass
+    P.roots = L.arena;  // each request's root node, kept by its greedy pass, at its root_base
     P.idle_timeout_ns = s->cfg.idle_timeout_ns > 0 ? s->cfg.idle_timeout_ns : 20000000000ll;
     P.cancel = s->cfg.cancel;
     P.sm_nodes = L.sm_nodes;
@@ -225,11 +226,13 @@ int admit(Lane &L) {
         L.arena_used += r->bytes;
         const size_t off_bytes = up(sizeof(int32_t) * ((size_t)r->n + 1));
         const size_t adj_bytes = up(sizeof(int32_t) * std::max<size_t>(r->adj.size(), 1));
+        const size_t cover_bytes = up(sizeof(int32_t) * std::max<size_t>(r->n, 1));
         Problem *p = stage_problem(L, slot);
         std::memset(p, 0, sizeof(Problem));
         p->off_base = (int64_t)(base / 4);
         p->adj_base = (int64_t)((base + off_bytes) / 4);
         p->cover_base = (int64_t)((base + off_bytes + adj_bytes) / 4);
+        p->root_base = (int64_t)(base + off_bytes + adj_bytes + cover_bytes);
         p->n = r->n;
         p->kind = r->kind;
         p->k = r->k;
@@ -630,7 +633,7 @@ int vc_server_submit(vc_server *s, const vc_graph *g, int32_t kind, int32_t k, u
     else r->off.assign(g->offsets, g->offsets + g->n + 1);
     if (len > 0) r->adj.assign(g->neighbors, g->neighbors + len);
     r->bytes = up(sizeof(int32_t) * ((size_t)r->n + 1)) + up(sizeof(int32_t) * std::max<size_t>(len, 1)) +
-               up(sizeof(int32_t) * std::max<size_t>(r->n, 1));
+               up(sizeof(int32_t) * std::max<size_t>(r->n, 1)) + up((size_t)s->lane[r->lane].eb);  // + root entry
     if (r->bytes > s->lane[r->lane].arena_bytes) {
         delete r;
         return VC_EINVAL;
