@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--serve-workers", type=int, default=0,
                     help="CSR-walk workers of the server (0: its default split of the SMs)")
     ap.add_argument("--serve-csr-only", action="store_true", help="serve every request on CSR walks")
+    ap.add_argument("--serve-classes", action="store_true", help="serve graphs of <= 128 vertices on bit rows")
+    ap.add_argument("--serve-threads", type=int, default=0, help="threads per CSR-walk worker of the server")
     ap.add_argument("--serve-only", action="store_true", help="run only the served-stream leg")
     return ap.parse_args()
 
@@ -84,6 +86,10 @@ def serve_config(vc, a):
         kw["num_workers"] = a.serve_workers
     if a.serve_csr_only:
         kw["bit_rows"] = -1
+    if a.serve_classes:
+        kw["bit_rows"] = 1
+    if a.serve_threads > 0:
+        kw["worker_threads"] = a.serve_threads
     return vc.make_config(**kw) if kw else None
 
 
