@@ -85,9 +85,9 @@ typedef struct {
                                    the server, the batch plan and vc_mvc_noalloc keep the node in shared
                                    memory. */
     int32_t bit_rows;           /* adjacency lookups of one-warp, shared-memory workers: 0 = bit rows of the
-                                   adjacency matrix in shared memory for graphs of at most 128 vertices,
-                                   else CSR walks; 1 = bit rows, also for graphs of up to 256 vertices
-                                   (VC_EINVAL when the launch does not qualify); -1 = CSR walks.  Same answers and reduced
+                                   adjacency matrix in shared memory for graphs of at most 256 vertices,
+                                   else CSR walks; 1 = bit rows required (VC_EINVAL when the launch does
+                                   not qualify); -1 = CSR walks.  Same answers and reduced
                                    degree arrays either way.  vc_mvc, vc_pvc, vc_mvc_batch, vc_greedy,
                                    vc_reduce_node and the batch plan honour it; the server walks the
                                    CSR unless bit_rows = 1 (then graphs of at most 128 vertices run on

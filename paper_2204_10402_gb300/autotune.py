@@ -9,8 +9,8 @@ Knobs (all fields of vc_config, include/vc.h):
                       neighbour lists (1), nothing (-1)
   node_in_global      placement of the current node (Sec. IV-E's two kernel versions): shared
                       memory when it fits (0) or global memory (1)
-  bit_rows            adjacency lookups: bit rows for graphs up to 128 vertices (0), also up to
-                      256 (1), CSR walks (-1)
+  bit_rows            adjacency lookups: bit rows for graphs up to 256 vertices where they can
+                      run (0), bit rows required (1), CSR walks (-1)
 
 Search: coordinate descent from the library's defaults -- each knob in turn is set to the value
 with the lowest measured traversal time while the others stay fixed; two sweeps.  Results are

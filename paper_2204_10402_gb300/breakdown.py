@@ -84,11 +84,14 @@ def run(graphs: int, clique: int, lib_path: str | None = None) -> dict:
         g, _ = G.gnp_with_planted_clique(clique, 0.05, c, 0)
         off = torch.from_numpy(g.offsets).cuda()
         nbr = torch.from_numpy(g.neighbors).cuda()
-        a = vc.mvc(off, nbr)
-        torch.cuda.synchronize()
-        out["clique"] = summarise(a.stats, vc.last_sm_nodes())
-        out["clique"]["workload"] = f"G({clique}, 0.05) + planted K_{c}, seed 0, one instance"
-        out["clique"]["mvc"] = a.value
+        # the default workers (bit rows up to 256 vertices), then CSR walks on the same instance
+        for key, cfg in (("clique", None), ("clique_csr", vc.make_config(bit_rows=-1))):
+            a = vc.mvc(off, nbr, config=cfg)
+            torch.cuda.synchronize()
+            out[key] = summarise(a.stats, vc.last_sm_nodes())
+            out[key]["workload"] = (f"G({clique}, 0.05) + planted K_{c}, seed 0, one instance"
+                                    + (", CSR walks" if cfg is not None else ""))
+            out[key]["mvc"] = a.value
     return out
 
 

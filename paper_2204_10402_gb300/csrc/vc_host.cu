@@ -227,9 +227,9 @@ int run(Workspace &ws, const Spec &spec, const vc_config *cfg_in, cudaStream_t s
         smem = smem_bytes_gm(csr_words);
     }
     if (smem > ws.smem_optin) return VC_EINVAL;  // graph too large for a shared-memory degree array
-    // Bit-row workers: one warp per worker, node in shared memory, n_max <= 128.
+    // Bit-row workers: one warp per worker, node in registers, n_max <= 256.
     int nw = 0;
-    if (cfg.bit_rows >= 0 && !gm && wt == 32) nw = rows_words_for(n_max, cfg.bit_rows > 0);
+    if (cfg.bit_rows >= 0 && !gm && wt == 32) nw = rows_words_for(n_max);
     if (cfg.bit_rows > 0 && nw == 0) return VC_EINVAL;
     if (nw > 0 && smem_bytes_for(n_max, wbytes, csr_words, nw) <= ws.smem_optin)
         smem = smem_bytes_for(n_max, wbytes, csr_words, nw);
@@ -609,7 +609,7 @@ int vc_reduce_node(const vc_graph *g, int32_t *deg, int32_t *S, int32_t *m, int3
     const bool gm = c.node_in_global > 0 || (c.node_in_global == 0 && smem > ws->smem_optin);
     if (gm) smem = smem_bytes_gm(0);
     if (smem > ws->smem_optin) return VC_EINVAL;
-    int nw = (c.bit_rows >= 0 && !gm && wt == 32) ? rows_words_for(g->n, c.bit_rows > 0) : 0;
+    int nw = (c.bit_rows >= 0 && !gm && wt == 32) ? rows_words_for(g->n) : 0;
     if (c.bit_rows > 0 && nw == 0) return VC_EINVAL;
     if (nw > 0) smem = smem_bytes_for(g->n, width / 8, 0, nw);
     cudaStream_t s = (cudaStream_t)stream;

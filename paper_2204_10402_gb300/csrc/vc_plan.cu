@@ -98,8 +98,8 @@ int vc_plan_create_mvc_batch(int32_t G, const int32_t *vtx, const int32_t *edge,
     pl->wt = cfg.worker_threads ? cfg.worker_threads : tuned.worker_threads;
     const int32_t csr_words = default_csr_words(n_max, cfg.stage_csr);
     pl->smem = smem_bytes_for(n_max, pl->width / 8, csr_words);
-    // Bit-row workers as in vc_mvc_batch: one warp per worker and n_max <= 128.
-    pl->nw = (cfg.bit_rows >= 0 && pl->wt == 32) ? rows_words_for(n_max, cfg.bit_rows > 0) : 0;
+    // Bit-row workers as in vc_mvc_batch: one warp per worker and n_max <= 256.
+    pl->nw = (cfg.bit_rows >= 0 && pl->wt == 32) ? rows_words_for(n_max) : 0;
     if (cfg.bit_rows > 0 && pl->nw == 0) {
         delete pl;
         return VC_EINVAL;

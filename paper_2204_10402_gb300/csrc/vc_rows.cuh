@@ -7,7 +7,9 @@
 // uniform bit masks over all vertices:
 //   live    vertices not in S
 //   pend    vertices chosen to enter S and not yet removed (a pass's proposals, a branch)
-//   dirty2  vertices whose degree changed since the last degree-two-triangle pass
+// Each lane also keeps one bit per own vertex (bit k: vertex 32k + l) marking a degree change since
+// the last degree-two-triangle pass; kept per lane instead of as NW uniform words, it frees NW - 1
+// registers, which lets 24 instead of 20 eight-word workers share an SM without more spills.
 // The read-only adjacency is staged in shared memory as one NW-word bit row per vertex, with each
 // vertex's input degree beside it.  Rule scans, removals and the argmax are lane-parallel bit
 // operations closed by warp votes and reductions: no degree array in shared memory, no atomics.
@@ -38,7 +40,7 @@ struct RowWorker {
     int32_t dg[NW];        // degree of vertex 32k + lane; -1 once in S (and beyond n)
     uint32_t live[NW];     // uniform
     uint32_t pend[NW];     // uniform
-    uint32_t dirty2[NW];   // uniform
+    uint32_t dl;           // per lane: bit k set when vertex 32k + lane changed since the last triangle pass
     int32_t S, m, branch, problem;
     int32_t maxdeg;        // an upper bound on the largest live degree (degrees only fall)
     // ---- statistics since the last flush into the shared tallies ----
@@ -67,10 +69,11 @@ struct RowWorker {
         branch = -1;
         problem = 0;
         maxdeg = 0;
+        dl = 0u;
 #pragma unroll
         for (int k = 0; k < NW; ++k) {
             dg[k] = -1;
-            live[k] = pend[k] = dirty2[k] = 0u;
+            live[k] = pend[k] = 0u;
         }
     }
 
@@ -187,8 +190,9 @@ struct RowWorker {
         branch = -1;
         problem = c.index;
         node_loaded(c);
+        dl = 0u;
 #pragma unroll
-        for (int k = 0; k < NW; ++k) dirty2[k] = live[k];
+        for (int k = 0; k < NW; ++k) dl |= (uint32_t)(dg[k] >= 0) << k;
     }
 
     // An entry from a stack or the worklist (loads through L2: the producer may be another SM).
@@ -206,8 +210,8 @@ struct RowWorker {
             const int v = 32 * k + lane;
             dg[k] = v < n_cap ? (int)__ldcg(s + v) : -1;
             pend[k] = 0u;
-            dirty2[k] = 0u;
         }
+        dl = 0u;
     }
 
     // Writes the node as an entry whose header's branch field is `br`.
@@ -235,8 +239,9 @@ struct RowWorker {
         branch = -1;
         problem = c.index;
         node_loaded(c);
+        dl = 0u;
 #pragma unroll
-        for (int k = 0; k < NW; ++k) dirty2[k] = all_dirty ? live[k] : 0u;
+        for (int k = 0; k < NW; ++k) dl |= (uint32_t)(all_dirty && dg[k] >= 0) << k;
     }
     __device__ void save_plain(const Ctx &c, int32_t *deg) const {
 #pragma unroll
@@ -286,8 +291,9 @@ struct RowWorker {
             for (int k = 0; k < NW; ++k) {
                 const uint32_t hit = r[k] & nl[k];
                 const bool mine = (pend[k] >> lane) & 1u;
-                dg[k] = mine ? -1 : dg[k] - (int)((hit >> lane) & 1u);
-                dirty2[k] |= hit;
+                const uint32_t b = (hit >> lane) & 1u;
+                dg[k] = mine ? -1 : dg[k] - (int)b;
+                dl |= b << k;
                 du += __popc(hit);
                 live[k] = nl[k];
                 pend[k] = 0u;
@@ -310,7 +316,7 @@ struct RowWorker {
                 changed = nd != dg[k];
                 dg[k] = nd;
             }
-            dirty2[k] |= __ballot_sync(kFull, changed);
+            dl |= (uint32_t)changed << k;
         }
         int sum = 0, mx = 0;
 #pragma unroll
@@ -400,10 +406,10 @@ struct RowWorker {
 #pragma unroll
         for (int k = 0; k < NW; ++k) {
             d2[k] = __ballot_sync(kFull, dg[k] == 2);
-            cand[k] = d2[k] & dirty2[k];
-            dirty2[k] = 0u;
+            cand[k] = __ballot_sync(kFull, dg[k] == 2 && ((dl >> k) & 1u));
             any |= cand[k];
         }
+        dl = 0u;
         ++passes;
         VC_CYC_INC(*this, kPTriCount);
         if (any == 0u) {  // nothing to look at: pend stays empty

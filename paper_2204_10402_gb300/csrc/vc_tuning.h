@@ -42,12 +42,13 @@ VC_HD inline int32_t default_worklist_capacity(int32_t entry_bytes, int32_t want
     return (int32_t)cap;
 }
 
-// Bit-row workers: words per adjacency row for graphs of at most n_max vertices (0 = none).
-// By default only up to 4 words: on the planted-clique graphs (n = 160-200, p = 0.05) 8-word rows
-// ran 1.5-2.3x slower than CSR walks (sparse rows, and fewer workers fit), so they are used only
-// on request (`forced`).
-VC_HD inline int32_t rows_words_for(int32_t n_max, bool forced = false) {
-    return n_max <= 32 ? 1 : n_max <= 64 ? 2 : n_max <= 128 ? 4 : (forced && n_max <= 256) ? 8 : 0;
+// Bit-row workers: words per adjacency row for graphs of at most n_max vertices (0 = none; such
+// graphs use CSR walks).  Eight-word rows against CSR walks on graphs of 129-256 vertices, kernel
+// times on a GB300: planted clique G(200, .05) + K_12 967 / 1279 ms, G(180, .05) + K_11 191 / 249 ms,
+// G(n, p) n 150-256 1.19-1.32x faster, Chung-Lu n 180-256 1.8-1.9x, a 512-graph G(n, .01-.02)
+// batch with n 129-256 31.9 / 41.0 ms.
+VC_HD inline int32_t rows_words_for(int32_t n_max) {
+    return n_max <= 32 ? 1 : n_max <= 64 ? 2 : n_max <= 128 ? 4 : n_max <= 256 ? 8 : 0;
 }
 // Shared-memory CSR staging by default: the offsets (n+1 ints) of graphs with up to
 // kOffsetStageN vertices; nothing for larger graphs (their workers share the CSR through L1).

@@ -444,16 +444,16 @@ def test_planted_clique_pvc_three_columns(vc):
             assert a.cover_size <= k
 
 
-@pytest.mark.parametrize("n,bit_rows", [(180, 1), (200, 0), (180, -1)])
+@pytest.mark.parametrize("n,bit_rows", [(180, 1), (200, 0), (180, -1), (200, -1)])
 def test_planted_clique_stored_answers(vc, n, bit_rows):
     # Sizes the oracle needs minutes for (answers stored by tests/golden/make_clique_golden.py);
-    # 8-word bit rows on request (bit_rows = 1), CSR walks by default and with bit_rows = -1.
+    # 8-word bit rows by default and on request (bit_rows = 1), CSR walks with bit_rows = -1.
     c, m, want = load_clique_golden()[n]
     g, _ = G.gnp_with_planted_clique(n, 0.05, c, 0)
     assert g.m == m
     a = vc.mvc(g.offsets, g.neighbors, config=vc.make_config(bit_rows=bit_rows))
     assert a.value == want
-    assert a.stats["bit_rows"] == (8 if bit_rows == 1 else 0)
+    assert a.stats["bit_rows"] == (0 if bit_rows < 0 else 8)
     check_cover(g, a.cover, want)
     assert vc.pvc(g.offsets, g.neighbors, want - 1, want_cover=False).value == 0
 

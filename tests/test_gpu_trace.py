@@ -2,7 +2,8 @@
 
 The instrumented library is built into a directory of its own and loaded by a child process
 (a process loads one build of the library).  Checks:
-  - its answers equal the oracle's (stored batch answers; the planted-clique instance solved here)
+  - its answers equal the oracle's (stored batch answers; the planted-clique instance solved here,
+    on bit rows and on CSR walks)
   - every activity slot that both workloads exercise is non-zero
   - the traced worker time and the traced cycles fit inside the kernel's duration x workers
   - the traced pass counts add up to the rule passes the product counters report
@@ -52,10 +53,12 @@ def test_trace_build_answers_match_oracle(traced):
     assert traced["batch"]["sizes"] == want
     c = round(25 * CLIQUE_N / 400)
     g, _ = G.gnp_with_planted_clique(CLIQUE_N, 0.05, c, 0)
-    assert traced["clique"]["mvc"] == oracle.mvc(g)[0]
+    want = oracle.mvc(g)[0]
+    assert traced["clique"]["mvc"] == want and traced["clique_csr"]["mvc"] == want
+    assert traced["clique"]["bit_rows"] == 4 and traced["clique_csr"]["bit_rows"] == 0
 
 
-@pytest.mark.parametrize("which", ["batch", "clique"])
+@pytest.mark.parametrize("which", ["batch", "clique", "clique_csr"])
 def test_trace_slots_consistent(traced, which):
     r = traced[which]
     assert r["nodes"] > 0 and r["kernel_ms"] > 0
