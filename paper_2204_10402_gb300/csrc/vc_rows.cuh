@@ -374,26 +374,46 @@ struct RowWorker {
         uint32_t prop[NW];
 #pragma unroll
         for (int w = 0; w < NW; ++w) prop[w] = 0u;
+        if constexpr (NW >= 8) {
+            // Eight-word rows: a dynamic loop over this lane's candidates (bit k: vertex 32k +
+            // lane) keeps the pass's code O(NW) instead of O(NW^2).  Unrolled, the rule passes
+            // missed the instruction cache (ncu: 3.1 no_instruction stalls per issue on the
+            // planted clique n = 160) and the planted clique n = 200 took 975 against 842 ms;
+            // for four-word rows the unrolled loop is 3 % faster on the 4096-graph batch.
+            uint32_t mine = 0u;
 #pragma unroll
-        for (int k = 0; k < NW; ++k) {
-            if (d1[k] == 0u) continue;
-            if ((d1[k] >> lane) & 1u) {
-                uint32_t r[NW];
-                row(32 * k + lane, r);
-                uint32_t nb_d1 = 0u, above = 0u;
+            for (int k = 0; k < NW; ++k) mine |= ((d1[k] >> lane) & 1u) << k;
+            while (mine) {
+                const int k = __ffs(mine) - 1;
+                mine &= mine - 1u;
+                degree_one_candidate(k, d1, prop);
+            }
+        } else {
 #pragma unroll
-                for (int w = 0; w < NW; ++w) {
-                    r[w] &= live[w];  // exactly one bit in all: u
-                    nb_d1 |= r[w] & d1[w];
-                    if (w > k) above |= r[w];
-                    else if (w == k) above |= r[w] & ~((2u << lane) - 1u);
-                }
-                if (!(nb_d1 && above))
-#pragma unroll
-                    for (int w = 0; w < NW; ++w) prop[w] |= r[w];
+            for (int k = 0; k < NW; ++k) {
+                if (d1[k] == 0u) continue;
+                if ((d1[k] >> lane) & 1u) degree_one_candidate(k, d1, prop);
             }
         }
         return finish(prop, kPDeg1, t0);
+    }
+
+    // Degree-one candidate 32k + lane: proposes its live neighbour unless that is a degree-one
+    // vertex of smaller id.
+    __device__ __forceinline__ void degree_one_candidate(int k, const uint32_t (&d1)[NW], uint32_t (&prop)[NW]) const {
+        uint32_t r[NW];
+        row(32 * k + lane, r);
+        uint32_t nb_d1 = 0u, above = 0u;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            r[w] &= live[w];  // exactly one bit in all: u
+            nb_d1 |= r[w] & d1[w];
+            if (w > k) above |= r[w];
+            else if (w == k) above |= r[w] & ~((2u << lane) - 1u);
+        }
+        if (!(nb_d1 && above))
+#pragma unroll
+            for (int w = 0; w < NW; ++w) prop[w] |= r[w];
     }
 
     // Degree-two-triangle: if N(v) = {u, x} (the two bits of row(v) & live) and ux is an edge (row(u)
@@ -419,37 +439,52 @@ struct RowWorker {
         uint32_t prop[NW];
 #pragma unroll
         for (int w = 0; w < NW; ++w) prop[w] = 0u;
+        if constexpr (NW >= 8) {  // one loop over this lane's candidates, as in the degree-one pass
+            uint32_t mine = 0u;
 #pragma unroll
-        for (int k = 0; k < NW; ++k) {
-            if (cand[k] == 0u) continue;
-            if ((cand[k] >> lane) & 1u) {
-                uint32_t r[NW];
-                row(32 * k + lane, r);
-                uint32_t tie = 0u;
-                int u = -1;
+            for (int k = 0; k < NW; ++k) mine |= ((cand[k] >> lane) & 1u) << k;
+            while (mine) {
+                const int k = __ffs(mine) - 1;
+                mine &= mine - 1u;
+                triangle_candidate(k, d2, prop);
+            }
+        } else {
 #pragma unroll
-                for (int w = 0; w < NW; ++w) {
-                    r[w] &= live[w];  // exactly two bits in all: u < x
-                    const uint32_t below = w < k ? ~0u : (w == k ? (1u << lane) - 1u : 0u);
-                    tie |= r[w] & d2[w] & below;
-                }
-#pragma unroll
-                for (int w = NW - 1; w >= 0; --w)
-                    if (r[w]) u = 32 * w + __ffs(r[w]) - 1;
-                if (!tie && u >= 0) {
-                    // ux is an edge iff row(u) meets {u, x} = r (u has no bit of its own): one row
-                    // load, no search for x (2 % faster on the batch than testing bit x of row(u))
-                    uint32_t ru[NW], hit = 0u;
-                    row(u, ru);
-#pragma unroll
-                    for (int w = 0; w < NW; ++w) hit |= ru[w] & r[w];
-                    if (hit)
-#pragma unroll
-                        for (int w = 0; w < NW; ++w) prop[w] |= r[w];
-                }
+            for (int k = 0; k < NW; ++k) {
+                if (cand[k] == 0u) continue;
+                if ((cand[k] >> lane) & 1u) triangle_candidate(k, d2, prop);
             }
         }
         return finish(prop, kPTri, t0);
+    }
+
+    // Triangle candidate 32k + lane: proposes its two live neighbours when they are adjacent and no
+    // degree-two vertex of the triangle has a smaller id.
+    __device__ __forceinline__ void triangle_candidate(int k, const uint32_t (&d2)[NW], uint32_t (&prop)[NW]) const {
+        uint32_t r[NW];
+        row(32 * k + lane, r);
+        uint32_t tie = 0u;
+        int u = -1;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            r[w] &= live[w];  // exactly two bits in all: u < x
+            const uint32_t below = w < k ? ~0u : (w == k ? (1u << lane) - 1u : 0u);
+            tie |= r[w] & d2[w] & below;
+        }
+#pragma unroll
+        for (int w = NW - 1; w >= 0; --w)
+            if (r[w]) u = 32 * w + __ffs(r[w]) - 1;
+        if (!tie && u >= 0) {
+            // ux is an edge iff row(u) meets {u, x} = r (u has no bit of its own): one row
+            // load, no search for x (2 % faster on the batch than testing bit x of row(u))
+            uint32_t ru[NW], hit = 0u;
+            row(u, ru);
+#pragma unroll
+            for (int w = 0; w < NW; ++w) hit |= ru[w] & r[w];
+            if (hit)
+#pragma unroll
+                for (int w = 0; w < NW; ++w) prop[w] |= r[w];
+        }
     }
 
     // High-degree: a vertex whose degree exceeds best-|S|-1 (MVC) or k-|S| (PVC) enters S.  Skipped
