@@ -411,16 +411,18 @@ __device__ int acquire(const Params &P, Wk &w) {
 // (32, 32) on one GB300.  More resident warps did not pay: 48, 40 and 32 registers with two or
 // four workers per block (40 to 64 warps per SM) ran 171, 180 and 250 ms against 171 ms for the
 // same build at 64 registers.  Eight-word bit-row workers (graphs of 129-256 vertices) declare 32
-// threads / 24 blocks instead: their node needs more registers, and at the 64-register cap they
+// threads / 28 blocks instead: their node needs more registers, and at the 64-register cap they
 // spilled 136 bytes and ran the planted clique G(200, 0.05) + K_12 in 1420 ms; at 128 / 96 / 85
 // registers (16 / 20 / 24 workers per SM) it took 1080 / 991 / 964 ms, against 1255 ms for CSR walks.
+// With the passes' dynamic candidate loops, 22 / 24 / 28 blocks (80, 80, 72 registers; 16-96 bytes
+// of spills) took 849 / 848 / 835 ms.
 constexpr int kMaxThreads(int wt) { return wt == 32 ? 64 : wt; }
 constexpr unsigned kSnapshotEvery = 16;  // nodes per re-read of the shared bounds (a power of two)
 constexpr int kMinBlocks(int wt) { return wt == 32 ? 16 : 1024 / wt; }
 // SERVE: the launch also takes requests from a server's ring (the instance the server launches);
 // batch launches use the instance without that path, which keeps their code smaller.
 template <typename W, int WT, bool GM, int NW, bool SERVE>
-__global__ void __launch_bounds__(NW == 8 ? 32 : kMaxThreads(WT), NW == 8 ? 24 : kMinBlocks(WT)) traverse_kernel(Params P) {
+__global__ void __launch_bounds__(NW == 8 ? 32 : kMaxThreads(WT), NW == 8 ? 28 : kMinBlocks(WT)) traverse_kernel(Params P) {
     extern __shared__ __align__(16) uint8_t smem[];
     using Wk = typename WorkerSel<W, WT, GM, NW>::type;
     Wk w(smem, P.n_max, P.csr_words, P.gstate + (size_t)blockIdx.x * (size_t)P.gstate_bytes);
