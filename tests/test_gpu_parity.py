@@ -281,6 +281,46 @@ def test_batch_adjacency_modes_match_stored_answers(vc, bit_rows):
         check_cover(g, covers[b.vtx[i]: b.vtx[i + 1]], want[i][2])
 
 
+def mid_size_graphs():
+    # 129-256 vertices (eight-word bit rows by default), trees the oracle finishes in under a second
+    out = [G.gnp(n, p, s) for n, p, s in [(140, 0.04, 11), (180, 0.025, 12), (230, 0.018, 13), (256, 0.015, 14),
+                                          (129, 0.05, 15)]]
+    out += [G.chung_lu(200, 6.0, 21), G.chung_lu(256, 9.0, 22)]
+    out.append(G.gnp_with_planted_clique(140, 0.05, 9, 0)[0])
+    return out
+
+
+@pytest.mark.parametrize("width", [32, 16])
+def test_mid_size_graphs_default_bit_rows(vc, width):
+    # The default workers for 129-256 vertices (eight-word rows) against the oracle, MVC and PVC at
+    # k = MVC - 1 / MVC, and against CSR walks (bit_rows = -1) on the same graphs.
+    for g in mid_size_graphs():
+        want, _, _ = oracle.mvc(g)
+        a = vc.mvc(g.offsets, g.neighbors, config=vc.make_config(width=width))
+        assert a.stats["bit_rows"] == 8, g.n
+        assert a.value == want, (g.n, g.m)
+        check_cover(g, a.cover, want)
+        csr = vc.mvc(g.offsets, g.neighbors, config=vc.make_config(width=width, bit_rows=-1))
+        assert csr.stats["bit_rows"] == 0 and csr.value == want
+        for k in (want - 1, want):
+            p = vc.pvc(g.offsets, g.neighbors, k, config=vc.make_config(width=width))
+            assert p.value == (1 if k >= want else 0), (g.n, k)
+            if p.value:
+                check_cover(g, p.cover, p.cover_size)
+                assert p.cover_size <= k
+
+
+def test_mid_size_batch_default_bit_rows(vc):
+    # A batch whose largest graph has 129-256 vertices runs on eight-word rows.
+    b = G.batch_gnp(64, first_seed=60000, n_lo=129, n_hi=256, p_lo=0.014, p_hi=0.02)
+    sizes, covers, st = vc.mvc_batch(b.vtx, b.edge, b.offsets, b.neighbors)
+    assert st["bit_rows"] == 8
+    for i, g in enumerate(b.graphs):
+        want, _, _ = oracle.mvc(g)
+        assert sizes[i] == want, i
+        check_cover(g, covers[b.vtx[i]: b.vtx[i + 1]], want)
+
+
 def load_batch_golden():
     import os
     rows = {}
