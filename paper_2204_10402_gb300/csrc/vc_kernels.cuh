@@ -324,26 +324,20 @@ __device__ __forceinline__ int serve_wait(const Params &P, int &arg) {
 // is claimed; see serve_wait).  Sec. IV-C: the search is over when
 // the worklist is empty and no worker holds work, i.e. when no work unit is left.
 template <bool SERVE, class Wk>
-__device__ int acquire(const Params &P, Wk &w, bool &first) {
+__device__ int acquire(const Params &P, Wk &w) {
     Control *ctrl = P.ctrl;
     if (w.tid == 0) {
         int result = 0, arg = 0;
+        // Unclaimed roots; a serving launch gets its problems through serve_wait instead (its slots
+        // hold no work until a request is claimed, and sweeping them cost every launch 16 K atomics).
         if (!(SERVE && P.serving)) {
-            // Roots: on its first call worker b takes root b, with no atomic (thousands of workers
-            // starting at once all found the shared counter below the count and raced on it); the
-            // counter hands out the roots beyond the grid.  A serving launch gets its problems
-            // through serve_wait instead.
-            const int32_t g0 = min(P.num_problems, (int32_t)gridDim.x);
-            if (first && (int32_t)blockIdx.x < g0 && ld_relaxed(&P.problems[blockIdx.x].units) > 0) {
-                result = 1;
-                arg = (int)blockIdx.x;
-            }
-            while (!result && ld_relaxed(&ctrl->next_root) < P.num_problems - g0) {
-                const int r = g0 + atomicAdd(&ctrl->next_root, 1);
+            while (ld_relaxed(&ctrl->next_root) < P.num_problems) {
+                const int r = atomicAdd(&ctrl->next_root, 1);
                 if (r >= P.num_problems) break;
                 if (ld_relaxed(&P.problems[r].units) > 0) {
                     result = 1;
                     arg = r;
+                    break;
                 }
             }
         }
@@ -390,7 +384,6 @@ __device__ int acquire(const Params &P, Wk &w, bool &first) {
         w.sc[kScB4] = result;
         w.sc[kScB5] = arg;
     }
-    first = false;
     w.sync();
     const int result = w.sc[kScB4];
     const int arg = w.sc[kScB5];
@@ -447,7 +440,6 @@ __global__ void __launch_bounds__(NW == 8 ? 32 : kMaxThreads(WT), NW == 8 ? 28 :
     int cur = -1;
     bool stop = false;
     bool fresh = true;  // the next node needs a fresh snapshot (its problem may be new)
-    bool first_acquire = true;
     uint32_t nn = 0;    // bit-row workers: nodes expanded (its low bits pace the periodic work)
     int32_t bound = 0;  // snapshot: best (MVC) or k (PVC), one value for a whole node (reading R3)
     int32_t fill = 0;   // snapshot: worklist entries waiting
@@ -475,7 +467,7 @@ __global__ void __launch_bounds__(NW == 8 ? 32 : kMaxThreads(WT), NW == 8 ? 28 :
             cur = -1;
             const unsigned long long t_wait = VC_TRACE_NOW();
             const long long t_acq = VC_CYC();
-            int got = acquire<SERVE>(P, w, first_acquire);
+            int got = acquire<SERVE>(P, w);
             fresh = true;
             VC_TRACE_ADD(w, kTWaitNs, t_wait);
             VC_CYC_ADD(w, kPAcquire, t_acq);
