@@ -13,7 +13,9 @@ namespace vc {
 //   n <= 64    4096 G(n,p), n 20-64           one warp, 32-bit entries, threshold 0.25
 //   n <= 128   4096 G(n,p), n 20-120          one warp, 32-bit entries, threshold 0.5 (with bit
 //                                             rows; 16-bit entries were best for CSR walks)
-//   n <= 400   planted-clique G(160/200, .05) one warp, 32-bit entries (1935 -> 1400 ms at n = 200)
+//   n <= 400   planted-clique G(160/200, .05) one warp, 32-bit entries (1935 -> 1400 ms at n = 200
+//                                             with CSR walks; up to 256 vertices the one-warp
+//                                             workers use eight-word bit rows, rows_words_for)
 //   n <= 1200  two warps; n <= 2560 four warps; larger: eight warps, threshold 0.25
 //   worklist capacity: 512K entries for n <= 128 (169 -> 167 ms on the 20-120 batch), 256K
 //   elsewhere (the 20-64 batch: 2.70 ms at 512K, 2.21 ms at 256K)
