@@ -323,6 +323,9 @@ __device__ __forceinline__ int serve_wait(const Params &P, int &arg) {
 // 1 (a root is loaded), 2 (a worklist entry is loaded) or, in serving launches, 3 (a new request
 // is claimed; see serve_wait).  Sec. IV-C: the search is over when
 // the worklist is empty and no worker holds work, i.e. when no work unit is left.
+constexpr int kAwakeWorkers = 608;       // idle bit-row workers that poll at once in a small search
+constexpr uint32_t kParkBeats = 64;      // heartbeat (busy workers bump it every 32 nodes) that ends parking
+constexpr unsigned kParkNs = 16384;      // a parked worker's poll interval
 template <bool SERVE, class Wk>
 __device__ int acquire(const Params &P, Wk &w) {
     Control *ctrl = P.ctrl;
@@ -351,6 +354,14 @@ __device__ int acquire(const Params &P, Wk &w) {
             uint64_t t0 = globaltimer_ns();
             uint32_t beat = ld_relaxed_u32(&ctrl->heartbeat);
             unsigned sleep_ns = 64 + (blockIdx.x & 63);
+            if constexpr (Wk::kRowWords > 0) {
+                // While the search is small (heartbeat below 64: fewer than about 2 K nodes so far),
+                // bit-row workers beyond the first kAwakeWorkers start parked, polling every 16 us:
+                // thousands of pollers racing for the few entries of a small search slowed the
+                // workers that had work (G(60, 0.10): 113 -> 80 us of traversal; the 4096-graph
+                // batch and the planted cliques unchanged).  They join once the heartbeat grows.
+                if ((int)blockIdx.x >= kAwakeWorkers && beat < kParkBeats) sleep_ns = kParkNs;
+            }
             for (;;) {
                 const long long pos = wl_take(P);
                 if (pos >= 0) {
@@ -379,6 +390,9 @@ __device__ int acquire(const Params &P, Wk &w) {
 #endif
                 __nanosleep(sleep_ns);
                 if (sleep_ns < 8192) sleep_ns += sleep_ns >> 1;
+                if constexpr (Wk::kRowWords > 0) {
+                    if (sleep_ns > 8192 && b >= kParkBeats) sleep_ns = 8192;
+                }
             }
         }
         w.sc[kScB4] = result;
