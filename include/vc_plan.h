@@ -43,6 +43,15 @@ int vc_plan_launch(vc_plan *plan, void *stream);
 int vc_plan_results(vc_plan *plan, void *stream, int32_t *sizes_out, int32_t *covers_out, int32_t covers_on_device,
                     vc_stats *stats);
 
+/* Per-graph completion of the last launch: waits for `stream`, then writes to done_ns_out (host,
+ * num_graphs entries) when each graph was answered, in nanoseconds of the GPU's global timer after
+ * the greedy pass's start (Sec. II-B); the time of the step's first kernel is the same up to a few
+ * microseconds.  A graph is answered when the greedy bound settles it or when the last piece of its
+ * search (root, worklist entry or local stack) is released (Sec. IV-C).  Every graph of a batched
+ * launch is returned with the whole launch: these times show how long each graph's own search
+ * lasted within it.  VC_EINVAL for a NULL argument. */
+int vc_plan_completion_ns(vc_plan *plan, void *stream, int64_t *done_ns_out);
+
 int vc_plan_destroy(vc_plan *plan);
 
 #ifdef __cplusplus

@@ -30,7 +30,7 @@ EXPORTED = ["vc_mvc", "vc_pvc", "vc_mvc_batch", "vc_greedy", "vc_reduce_node", "
             "vc_release", "vc_strerror", "vc_version", "vc_mvc_noalloc",
             "vc_server_create", "vc_server_submit", "vc_server_poll", "vc_server_release", "vc_server_drain",
             "vc_server_stats", "vc_server_destroy", "vc_plan_create_mvc_batch", "vc_plan_launch", "vc_plan_results",
-            "vc_plan_destroy", "vc_l2_copy_probe"]
+            "vc_plan_completion_ns", "vc_plan_destroy", "vc_l2_copy_probe"]
 NOALLOC_MAX_N = 512
 
 
@@ -136,6 +136,7 @@ def load(path: str | None = None):
     lib.vc_plan_create_mvc_batch.argtypes = [i32, P, P, P, P, i32, cp, ctypes.POINTER(ctypes.c_void_p)]
     lib.vc_plan_launch.argtypes = [P, P]
     lib.vc_plan_results.argtypes = [P, P, P, P, i32, sp]
+    lib.vc_plan_completion_ns.argtypes = [P, P, P]
     lib.vc_plan_destroy.argtypes = [P]
     lib.vc_l2_copy_probe.argtypes = [P, P, ctypes.c_size_t, i32, P]
     lib.vc_release.argtypes = []
@@ -145,7 +146,8 @@ def load(path: str | None = None):
     for name in ("vc_mvc", "vc_pvc", "vc_mvc_batch", "vc_greedy", "vc_reduce_node", "vc_last_sm_nodes",
                  "vc_release", "vc_version", "vc_mvc_noalloc", "vc_server_create", "vc_server_submit",
                  "vc_server_poll", "vc_server_release", "vc_server_drain", "vc_server_stats", "vc_server_destroy",
-                 "vc_plan_create_mvc_batch", "vc_plan_launch", "vc_plan_results", "vc_plan_destroy"):
+                 "vc_plan_create_mvc_batch", "vc_plan_launch", "vc_plan_results", "vc_plan_completion_ns",
+                 "vc_plan_destroy"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     _lib_path = os.path.abspath(path)
@@ -505,6 +507,13 @@ class BatchPlan:
                                          covers.ctypes.data if covers is not None else None, 0,
                                          ctypes.byref(st)), "vc_plan_results")
         return sizes[: self.G], covers, st.as_dict()
+
+    def completion_ms(self, stream=None) -> np.ndarray:
+        """Per graph of the last launch: when it was answered, in ms after the greedy pass's start
+        (vc_plan_completion_ns)."""
+        out = np.zeros(max(self.G, 1), dtype=np.int64)
+        _check(self._lib.vc_plan_completion_ns(self._h, _stream(stream), out.ctypes.data), "vc_plan_completion_ns")
+        return out[: self.G].astype(np.float64) * 1e-6
 
     def close(self):
         if getattr(self, "_h", None):

@@ -56,6 +56,7 @@ struct alignas(128) Problem {
     int32_t done;        // 1 once the last unit was released
     int32_t tag;         // serving: completion tag the host waits for (0 otherwise)
     int64_t root_base;   // byte offset of this problem's root entry in Params::roots
+    int64_t t_done_ns;   // %globaltimer when the problem was answered (0 until then)
 };
 
 // Launch-wide control block.  Words that many workers hit with atomics or polls each own a
@@ -71,6 +72,7 @@ struct alignas(128) Control {
     alignas(128) int32_t status;       // VC_OK, or the first error code raised by any worker
     int32_t num_problems;
     int32_t max_depth;
+    uint64_t t_launch_ns;  // %globaltimer at the greedy kernel's start (the reference of Problem::t_done_ns)
     int32_t dbg_site;     // debug builds (VC_DEBUG_CHECKS): first failed bounds check ...
     int32_t dbg_value;    // ... and the offending value
     unsigned long long nodes;

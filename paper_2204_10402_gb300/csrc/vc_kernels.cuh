@@ -124,12 +124,14 @@ __global__ void __launch_bounds__(WT) greedy_kernel(Params P) {
     w.sync();
     if (w.sc[kScB0] != VC_OK) return;
     w.dbg = P.ctrl;
+    if (blockIdx.x == 0 && w.tid == 0) P.ctrl->t_launch_ns = globaltimer_ns();
     for (int p = blockIdx.x; p < P.num_problems; p += gridDim.x) {
         Ctx c = make_ctx(P, p);
         const bool search = greedy_solve(P, w, c);
         if (w.tid == 0) {
             c.prob->units = search ? 1 : 0;
             c.prob->done = search ? 0 : 1;
+            if (!search) c.prob->t_done_ns = (int64_t)globaltimer_ns();  // answered by the greedy bound
             if (search) atomicAdd(&P.ctrl->units_total, 1);
         }
     }
@@ -199,6 +201,7 @@ __device__ __forceinline__ void release_unit(const Params &P, int32_t p) {
     Problem *pr = P.problems + p;
     __threadfence();
     if (atomicSub(&pr->units, 1) == 1) {
+        pr->t_done_ns = (int64_t)globaltimer_ns();
         st_release(&pr->done, 1);
         if (P.completion) {
             volatile int32_t *rec = P.completion + 4 * (size_t)p;

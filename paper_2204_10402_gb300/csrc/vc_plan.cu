@@ -277,6 +277,25 @@ int vc_plan_results(vc_plan *pl, void *stream, int32_t *sizes_out, int32_t *cove
     return VC_OK;
 }
 
+int vc_plan_completion_ns(vc_plan *pl, void *stream, int64_t *done_ns_out) {
+    if (!pl || !done_ns_out) return VC_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<Problem> probs((size_t)pl->G);
+    Control c;
+    if (cudaMemcpyAsync(probs.data(), pl->probs, sizeof(Problem) * (size_t)pl->G, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(&c, pl->ctrl, sizeof(Control), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return VC_ECUDA;
+    }
+    if (c.status != VC_OK) return c.status;
+    for (int32_t g = 0; g < pl->G; ++g) {
+        const int64_t t = probs[(size_t)g].t_done_ns;
+        done_ns_out[g] = t > 0 && (uint64_t)t >= c.t_launch_ns ? t - (int64_t)c.t_launch_ns : 0;
+    }
+    return VC_OK;
+}
+
 int vc_plan_destroy(vc_plan *pl) {
     if (!pl) return VC_EINVAL;
     if (pl->exec) cudaGraphExecDestroy(pl->exec);

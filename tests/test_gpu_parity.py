@@ -461,6 +461,27 @@ def test_batch_plan_graph_replay(vc):
         vc.BatchPlan(pb.vtx, pb.edge, pb.offsets, nb)
 
 
+def test_batch_plan_completion_times(vc):
+    # When each graph of a launch was answered: MVC needs a search for every graph with an edge
+    # (the greedy bound alone proves no minimum), so each answer comes after the greedy pass began
+    # and within the launch; the largest search (oracle nodes) ends no earlier than the median graph.
+    import os
+    import torch
+    b = G.batch_gnp(512)
+    plan = vc.BatchPlan(b.vtx, b.edge, torch.from_numpy(b.offsets).cuda(), torch.from_numpy(b.neighbors).cuda())
+    plan.launch()
+    sizes, _, st = plan.results()
+    t = plan.completion_ms()
+    plan.close()
+    assert t.shape == (512,) and (t >= 0).all()
+    has_edges = np.array([g.m > 0 for g in b.graphs])
+    assert (t[has_edges] > 0).all()
+    assert t.max() <= st["kernel_ms"] + 5.0
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "batch4096_mvc.txt")
+    nodes = np.array([int(l.split()[4]) for l in open(path) if not l.startswith("#")][:512])
+    assert t[int(np.argmax(nodes))] >= np.median(t)
+
+
 def load_clique_golden():
     import os
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "planted_clique_mvc.txt")
