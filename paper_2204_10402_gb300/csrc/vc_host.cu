@@ -263,10 +263,13 @@ int run(Workspace &ws, const Spec &spec, const vc_config *cfg_in, cudaStream_t s
     VC_RC(grow(ws.sm_nodes, sizeof(unsigned long long) * (size_t)kSmSlots));
     const size_t adj_len_at = sizeof(Problem) * (size_t)G;
     const size_t ctrl_at = (adj_len_at + sizeof(int64_t) * (size_t)G + 127) & ~size_t(127);
-    VC_RC(grow_pinned(ws, ctrl_at + sizeof(Control)));
+    const size_t smn_at = (ctrl_at + sizeof(Control) + 127) & ~size_t(127);
+    VC_RC(grow_pinned(ws, smn_at + sizeof(unsigned long long) * (size_t)kSmSlots));
     Problem *h_probs = reinterpret_cast<Problem *>(ws.pinned);
     int64_t *h_adj_len = reinterpret_cast<int64_t *>(static_cast<uint8_t *>(ws.pinned) + adj_len_at);
     Control *h_ctrl = reinterpret_cast<Control *>(static_cast<uint8_t *>(ws.pinned) + ctrl_at);
+    // per-SM node counts of the launch (vc_last_sm_nodes), staged in pinned memory like the rest
+    unsigned long long *smn = reinterpret_cast<unsigned long long *>(static_cast<uint8_t *>(ws.pinned) + smn_at);
     std::memcpy(h_probs, spec.probs.data(), sizeof(Problem) * (size_t)G);
     for (int g = 0; g < G; ++g) h_probs[g].root_base = (int64_t)g * eb;  // one root entry per problem
     std::memcpy(h_adj_len, spec.adj_len.data(), sizeof(int64_t) * (size_t)G);
@@ -364,15 +367,14 @@ int run(Workspace &ws, const Spec &spec, const vc_config *cfg_in, cudaStream_t s
     if (cover_out && spec.total_vertices > 0)
         VC_CK(cudaMemcpyAsync(cover_out, ws.cover.p, sizeof(int32_t) * spec.total_vertices,
                               cover_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
-    std::vector<unsigned long long> smn(kSmSlots, 0);
     if (spec.search)
-        VC_CK(cudaMemcpyAsync(smn.data(), P.sm_nodes, sizeof(unsigned long long) * kSmSlots, cudaMemcpyDeviceToHost, s));
+        VC_CK(cudaMemcpyAsync(smn, P.sm_nodes, sizeof(unsigned long long) * kSmSlots, cudaMemcpyDeviceToHost, s));
     VC_CK(cudaStreamSynchronize(s));
     if (spec.search) {
         int used = ws.sms;
         for (int i = 0; i < kSmSlots; ++i)
             if (smn[i]) used = std::max(used, i + 1);
-        ws.last_sm_nodes.assign(smn.begin(), smn.begin() + used);
+        ws.last_sm_nodes.assign(smn, smn + used);
     }
 
     res.probs.assign(h_probs, h_probs + G);
