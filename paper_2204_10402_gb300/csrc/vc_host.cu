@@ -21,6 +21,7 @@ namespace {
 
 constexpr int kMaxDevices = 64;
 constexpr size_t kStackBudget = size_t(8) << 30;  // stacks beyond this size trigger a tighter depth
+constexpr size_t kBounceBytes = size_t(256) << 10;  // host arrays up to this size bounce through pinned memory
 constexpr int64_t kMinCappedDepth = 256;           // smallest per-worker depth worth a capped launch
 constexpr int64_t kDefaultIdleTimeoutNs = 20000000000ll;
 
@@ -264,7 +265,15 @@ int run(Workspace &ws, const Spec &spec, const vc_config *cfg_in, cudaStream_t s
     const size_t adj_len_at = sizeof(Problem) * (size_t)G;
     const size_t ctrl_at = (adj_len_at + sizeof(int64_t) * (size_t)G + 127) & ~size_t(127);
     const size_t smn_at = (ctrl_at + sizeof(Control) + 127) & ~size_t(127);
-    VC_RC(grow_pinned(ws, smn_at + sizeof(unsigned long long) * (size_t)kSmSlots));
+    // Small host arrays (a single request's CSR and cover) bounce through the same pinned region:
+    // a copy from or to pageable memory would be staged by the driver and synchronise by itself.
+    const size_t in_bytes = sizeof(int32_t) * (size_t)(spec.total_offsets + std::max<int64_t>(spec.total_adj, 0));
+    const size_t out_bytes = sizeof(int32_t) * (size_t)std::max<int64_t>(spec.total_vertices, 0);
+    const bool bounce_in = !spec.on_device && in_bytes <= kBounceBytes;
+    const bool bounce_out = cover_out && !cover_on_device && out_bytes > 0 && out_bytes <= kBounceBytes;
+    const size_t in_at = (smn_at + sizeof(unsigned long long) * (size_t)kSmSlots + 127) & ~size_t(127);
+    const size_t out_at = (in_at + (bounce_in ? in_bytes : 0) + 127) & ~size_t(127);
+    VC_RC(grow_pinned(ws, out_at + (bounce_out ? out_bytes : 0)));
     Problem *h_probs = reinterpret_cast<Problem *>(ws.pinned);
     int64_t *h_adj_len = reinterpret_cast<int64_t *>(static_cast<uint8_t *>(ws.pinned) + adj_len_at);
     Control *h_ctrl = reinterpret_cast<Control *>(static_cast<uint8_t *>(ws.pinned) + ctrl_at);
@@ -278,10 +287,18 @@ int run(Workspace &ws, const Spec &spec, const vc_config *cfg_in, cudaStream_t s
     if (!spec.on_device) {
         VC_RC(grow(ws.csr_off, sizeof(int32_t) * (size_t)std::max<int64_t>(spec.total_offsets, 1)));
         VC_RC(grow(ws.csr_adj, sizeof(int32_t) * (size_t)std::max<int64_t>(spec.total_adj, 1)));
-        VC_CK(cudaMemcpyAsync(ws.csr_off.p, spec.offsets, sizeof(int32_t) * spec.total_offsets,
+        const int32_t *src_off = spec.offsets, *src_adj = spec.neighbors;
+        if (bounce_in) {
+            int32_t *b = reinterpret_cast<int32_t *>(static_cast<uint8_t *>(ws.pinned) + in_at);
+            std::memcpy(b, spec.offsets, sizeof(int32_t) * (size_t)spec.total_offsets);
+            if (spec.total_adj > 0) std::memcpy(b + spec.total_offsets, spec.neighbors, sizeof(int32_t) * (size_t)spec.total_adj);
+            src_off = b;
+            src_adj = b + spec.total_offsets;
+        }
+        VC_CK(cudaMemcpyAsync(ws.csr_off.p, src_off, sizeof(int32_t) * spec.total_offsets,
                               cudaMemcpyHostToDevice, s));
         if (spec.total_adj > 0)
-            VC_CK(cudaMemcpyAsync(ws.csr_adj.p, spec.neighbors, sizeof(int32_t) * spec.total_adj,
+            VC_CK(cudaMemcpyAsync(ws.csr_adj.p, src_adj, sizeof(int32_t) * spec.total_adj,
                                   cudaMemcpyHostToDevice, s));
         d_off = static_cast<const int32_t *>(ws.csr_off.p);
         d_adj = static_cast<const int32_t *>(ws.csr_adj.p);
@@ -364,12 +381,14 @@ int run(Workspace &ws, const Spec &spec, const vc_config *cfg_in, cudaStream_t s
 
     VC_CK(cudaMemcpyAsync(h_probs, d_probs, sizeof(Problem) * (size_t)G, cudaMemcpyDeviceToHost, s));
     VC_CK(cudaMemcpyAsync(h_ctrl, d_ctrl, sizeof(Control), cudaMemcpyDeviceToHost, s));
+    int32_t *cover_bounce = bounce_out ? reinterpret_cast<int32_t *>(static_cast<uint8_t *>(ws.pinned) + out_at) : nullptr;
     if (cover_out && spec.total_vertices > 0)
-        VC_CK(cudaMemcpyAsync(cover_out, ws.cover.p, sizeof(int32_t) * spec.total_vertices,
+        VC_CK(cudaMemcpyAsync(cover_bounce ? cover_bounce : cover_out, ws.cover.p, sizeof(int32_t) * spec.total_vertices,
                               cover_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
     if (spec.search)
         VC_CK(cudaMemcpyAsync(smn, P.sm_nodes, sizeof(unsigned long long) * kSmSlots, cudaMemcpyDeviceToHost, s));
     VC_CK(cudaStreamSynchronize(s));
+    if (cover_bounce) std::memcpy(cover_out, cover_bounce, out_bytes);
     if (spec.search) {
         int used = ws.sms;
         for (int i = 0; i < kSmSlots; ++i)
