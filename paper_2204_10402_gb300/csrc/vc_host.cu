@@ -318,7 +318,10 @@ int run(Workspace &ws, const Spec &spec, const vc_config *cfg_in, cudaStream_t s
     P.n_max = n_max;
     P.entry_bytes = eb;
     P.ctrl = d_ctrl;
-    P.cover = static_cast<int32_t *>(ws.cover.p);
+    // A device cover_out is written by the kernels themselves (the greedy pass writes every entry
+    // before any search records a better cover), which saves the copy at the end.
+    const bool direct_cover = cover_out && cover_on_device && spec.total_vertices > 0;
+    P.cover = direct_cover ? cover_out : static_cast<int32_t *>(ws.cover.p);
     P.wl_capacity = cap;
     P.wl_threshold = threshold;
     P.csr_words = csr_words;
@@ -382,9 +385,9 @@ int run(Workspace &ws, const Spec &spec, const vc_config *cfg_in, cudaStream_t s
     VC_CK(cudaMemcpyAsync(h_probs, d_probs, sizeof(Problem) * (size_t)G, cudaMemcpyDeviceToHost, s));
     VC_CK(cudaMemcpyAsync(h_ctrl, d_ctrl, sizeof(Control), cudaMemcpyDeviceToHost, s));
     int32_t *cover_bounce = bounce_out ? reinterpret_cast<int32_t *>(static_cast<uint8_t *>(ws.pinned) + out_at) : nullptr;
-    if (cover_out && spec.total_vertices > 0)
+    if (cover_out && spec.total_vertices > 0 && !direct_cover)
         VC_CK(cudaMemcpyAsync(cover_bounce ? cover_bounce : cover_out, ws.cover.p, sizeof(int32_t) * spec.total_vertices,
-                              cover_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+                              cudaMemcpyDeviceToHost, s));
     if (spec.search)
         VC_CK(cudaMemcpyAsync(smn, P.sm_nodes, sizeof(unsigned long long) * kSmSlots, cudaMemcpyDeviceToHost, s));
     VC_CK(cudaStreamSynchronize(s));
