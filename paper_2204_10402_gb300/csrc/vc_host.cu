@@ -36,6 +36,7 @@ struct Workspace {
     int sms = 0;
     int smem_optin = 0;
     DevBuf csr_off, csr_adj, problems, adj_len, ctrl, cover, stacks, wl_slots, wl_seq, sm_nodes, gstate, rows, roots;
+    DevBuf meta;  // run(): problem records, lengths, control block and per-SM counts, laid out as in `pinned`
     void *pinned = nullptr;
     size_t pinned_cap = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -115,7 +116,8 @@ int workspace(Workspace **out) {
 
 void free_workspace(Workspace &ws) {
     DevBuf *bufs[] = {&ws.csr_off, &ws.csr_adj, &ws.problems, &ws.adj_len, &ws.ctrl, &ws.cover,
-                      &ws.stacks, &ws.wl_slots, &ws.wl_seq, &ws.sm_nodes, &ws.gstate, &ws.rows, &ws.roots};
+                      &ws.stacks, &ws.wl_slots, &ws.wl_seq, &ws.sm_nodes, &ws.gstate, &ws.rows, &ws.roots,
+                      &ws.meta};
     for (DevBuf *b : bufs) {
         if (b->p) cudaFree(b->p);
         b->p = nullptr;
@@ -257,11 +259,11 @@ int run(Workspace &ws, const Spec &spec, const vc_config *cfg_in, cudaStream_t s
     }
 
     // ---- device buffers ----
-    VC_RC(grow(ws.problems, sizeof(Problem) * (size_t)G));
-    VC_RC(grow(ws.adj_len, sizeof(int64_t) * (size_t)G));
-    VC_RC(grow(ws.ctrl, sizeof(Control)));
     VC_RC(grow(ws.cover, sizeof(int32_t) * (size_t)std::max<int64_t>(spec.total_vertices, 1)));
-    VC_RC(grow(ws.sm_nodes, sizeof(unsigned long long) * (size_t)kSmSlots));
+    // The problem records, their adjacency lengths, the control block and the per-SM counts share
+    // one device buffer laid out like their pinned staging: one upload sets them all (the control
+    // block and the counts as zeros) and one download reads them back, instead of two copies and
+    // two memsets before the launch and three copies after it.
     const size_t adj_len_at = sizeof(Problem) * (size_t)G;
     const size_t ctrl_at = (adj_len_at + sizeof(int64_t) * (size_t)G + 127) & ~size_t(127);
     const size_t smn_at = (ctrl_at + sizeof(Control) + 127) & ~size_t(127);
@@ -273,6 +275,8 @@ int run(Workspace &ws, const Spec &spec, const vc_config *cfg_in, cudaStream_t s
     const bool bounce_out = cover_out && !cover_on_device && out_bytes > 0 && out_bytes <= kBounceBytes;
     const size_t in_at = (smn_at + sizeof(unsigned long long) * (size_t)kSmSlots + 127) & ~size_t(127);
     const size_t out_at = (in_at + (bounce_in ? in_bytes : 0) + 127) & ~size_t(127);
+    const size_t meta_bytes = smn_at + sizeof(unsigned long long) * (size_t)kSmSlots;
+    VC_RC(grow(ws.meta, meta_bytes));
     VC_RC(grow_pinned(ws, out_at + (bounce_out ? out_bytes : 0)));
     Problem *h_probs = reinterpret_cast<Problem *>(ws.pinned);
     int64_t *h_adj_len = reinterpret_cast<int64_t *>(static_cast<uint8_t *>(ws.pinned) + adj_len_at);
@@ -282,6 +286,8 @@ int run(Workspace &ws, const Spec &spec, const vc_config *cfg_in, cudaStream_t s
     std::memcpy(h_probs, spec.probs.data(), sizeof(Problem) * (size_t)G);
     for (int g = 0; g < G; ++g) h_probs[g].root_base = (int64_t)g * eb;  // one root entry per problem
     std::memcpy(h_adj_len, spec.adj_len.data(), sizeof(int64_t) * (size_t)G);
+    std::memset(h_ctrl, 0, sizeof(Control));
+    std::memset(smn, 0, sizeof(unsigned long long) * (size_t)kSmSlots);
 
     const int32_t *d_off = spec.offsets, *d_adj = spec.neighbors;
     if (!spec.on_device) {
@@ -303,11 +309,11 @@ int run(Workspace &ws, const Spec &spec, const vc_config *cfg_in, cudaStream_t s
         d_off = static_cast<const int32_t *>(ws.csr_off.p);
         d_adj = static_cast<const int32_t *>(ws.csr_adj.p);
     }
-    Problem *d_probs = static_cast<Problem *>(ws.problems.p);
-    Control *d_ctrl = static_cast<Control *>(ws.ctrl.p);
-    VC_CK(cudaMemcpyAsync(d_probs, h_probs, sizeof(Problem) * (size_t)G, cudaMemcpyHostToDevice, s));
-    VC_CK(cudaMemcpyAsync(ws.adj_len.p, h_adj_len, sizeof(int64_t) * (size_t)G, cudaMemcpyHostToDevice, s));
-    VC_CK(cudaMemsetAsync(d_ctrl, 0, sizeof(Control), s));
+    uint8_t *dm = static_cast<uint8_t *>(ws.meta.p);
+    Problem *d_probs = reinterpret_cast<Problem *>(dm);
+    const int64_t *d_adj_len = reinterpret_cast<const int64_t *>(dm + adj_len_at);
+    Control *d_ctrl = reinterpret_cast<Control *>(dm + ctrl_at);
+    VC_CK(cudaMemcpyAsync(dm, ws.pinned, meta_bytes, cudaMemcpyHostToDevice, s));
 
     Params P;
     std::memset(&P, 0, sizeof(P));
@@ -327,7 +333,7 @@ int run(Workspace &ws, const Spec &spec, const vc_config *cfg_in, cudaStream_t s
     P.csr_words = csr_words;
     P.idle_timeout_ns = cfg.idle_timeout_ns > 0 ? cfg.idle_timeout_ns : kDefaultIdleTimeoutNs;
     P.cancel = cfg.cancel;
-    P.sm_nodes = static_cast<unsigned long long *>(ws.sm_nodes.p);
+    P.sm_nodes = reinterpret_cast<unsigned long long *>(dm + smn_at);
     if (gm) {
         P.gstate_bytes = gstate_bytes_for(n_max, wbytes);
         VC_RC(grow(ws.gstate, (size_t)workers * (size_t)P.gstate_bytes));
@@ -342,8 +348,7 @@ int run(Workspace &ws, const Spec &spec, const vc_config *cfg_in, cudaStream_t s
     P.roots = static_cast<uint8_t *>(ws.roots.p);
 
     if (!cfg.skip_validation)
-        VC_RC(launch_validate(d_off, d_adj, d_probs, static_cast<const int64_t *>(ws.adj_len.p), G,
-                              spec.total_vertices, d_ctrl, s));
+        VC_RC(launch_validate(d_off, d_adj, d_probs, d_adj_len, G, spec.total_vertices, d_ctrl, s));
     // A single large graph's greedy pass is one worker's sequential rounds: it runs on a 512-thread
     // block whatever the traversal's worker size (Chung-Lu graphs of 1,000-3,000 vertices: 40 %
     // less greedy time than with their 128- or 256-thread workers).
@@ -376,20 +381,16 @@ int run(Workspace &ws, const Spec &spec, const vc_config *cfg_in, cudaStream_t s
         P.wl_slots = static_cast<uint8_t *>(ws.wl_slots.p);
         P.wl_seq = static_cast<uint32_t *>(ws.wl_seq.p);
         VC_RC(launch_init_worklist(P.wl_seq, cap, d_ctrl, s));
-        VC_CK(cudaMemsetAsync(P.sm_nodes, 0, sizeof(unsigned long long) * (size_t)kSmSlots, s));
         VC_CK(cudaEventRecord(ws.ev0, s));
         VC_RC(L.traverse(wt, workers, smem, s, P));
         VC_CK(cudaEventRecord(ws.ev1, s));
     }
 
-    VC_CK(cudaMemcpyAsync(h_probs, d_probs, sizeof(Problem) * (size_t)G, cudaMemcpyDeviceToHost, s));
-    VC_CK(cudaMemcpyAsync(h_ctrl, d_ctrl, sizeof(Control), cudaMemcpyDeviceToHost, s));
+    VC_CK(cudaMemcpyAsync(ws.pinned, dm, meta_bytes, cudaMemcpyDeviceToHost, s));
     int32_t *cover_bounce = bounce_out ? reinterpret_cast<int32_t *>(static_cast<uint8_t *>(ws.pinned) + out_at) : nullptr;
     if (cover_out && spec.total_vertices > 0 && !direct_cover)
         VC_CK(cudaMemcpyAsync(cover_bounce ? cover_bounce : cover_out, ws.cover.p, sizeof(int32_t) * spec.total_vertices,
                               cudaMemcpyDeviceToHost, s));
-    if (spec.search)
-        VC_CK(cudaMemcpyAsync(smn, P.sm_nodes, sizeof(unsigned long long) * kSmSlots, cudaMemcpyDeviceToHost, s));
     VC_CK(cudaStreamSynchronize(s));
     if (cover_bounce) std::memcpy(cover_out, cover_bounce, out_bytes);
     if (spec.search) {
