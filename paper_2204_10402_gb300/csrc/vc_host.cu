@@ -35,7 +35,7 @@ struct Workspace {
     int device = -1;
     int sms = 0;
     int smem_optin = 0;
-    DevBuf csr_off, csr_adj, problems, adj_len, ctrl, cover, stacks, wl_slots, wl_seq, sm_nodes, gstate, rows, roots;
+    DevBuf csr_off, csr_adj, problems, adj_len, ctrl, cover, stacks, wl_slots, wl_seq, gstate, rows, roots;
     DevBuf meta;  // run(): problem records, lengths, control block and per-SM counts, laid out as in `pinned`
     void *pinned = nullptr;
     size_t pinned_cap = 0;
@@ -116,7 +116,7 @@ int workspace(Workspace **out) {
 
 void free_workspace(Workspace &ws) {
     DevBuf *bufs[] = {&ws.csr_off, &ws.csr_adj, &ws.problems, &ws.adj_len, &ws.ctrl, &ws.cover,
-                      &ws.stacks, &ws.wl_slots, &ws.wl_seq, &ws.sm_nodes, &ws.gstate, &ws.rows, &ws.roots,
+                      &ws.stacks, &ws.wl_slots, &ws.wl_seq, &ws.gstate, &ws.rows, &ws.roots,
                       &ws.meta};
     for (DevBuf *b : bufs) {
         if (b->p) cudaFree(b->p);
